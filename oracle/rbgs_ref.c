@@ -1,0 +1,170 @@
+/*
+ * Oracle for the red-black Gauss-Seidel (RBGS) solve of the 2D Poisson equation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct CPU
+ * statement of what the GPU path computes.  Only the test suite, the smoke check and
+ * the benchmark's CPU-baseline leg may build, load or call it; the library under
+ * paper_2607_01735_gb300/ never does, and this file shares no code with it.
+ *
+ * Build: gcc -O2 -ffp-contract=off (IEEE binary64 / binary32, round to nearest even,
+ * no fused multiply-add, so every operation below is one correctly rounded op).
+ *
+ * Problem (Section 2 of the paper): Poisson's equation with Dirichlet data on the unit
+ * square, discretised on a uniform grid with h = 1/(N+1).  We use the -Lap u = f sign
+ * (the paper writes Lap u = f, i.e. the same problem with f -> -f), so the 5-point
+ * update of Eq. (1) reads
+ *
+ *     u_ij <- (h^2 f_ij + u_{i-1,j} + u_{i+1,j} + u_{i,j-1} + u_{i,j+1}) * 0.25
+ *
+ * summed left to right in exactly that order.  Multiplying by 0.25 equals dividing by
+ * 4 in IEEE arithmetic (both are the correctly rounded value of the same real number).
+ *
+ * Colouring (Section 2): a point is red when i + j is even, black otherwise, with the
+ * boundary ring at index 0 and N+1 and the interior 1-based.  One sweep updates every
+ * red point, then every black point (Algorithm 1 / Algorithm 2: red then black per
+ * iteration).  A sweep count of n means n red+black pairs.
+ *
+ * Storage here is the natural row-major (ni+2) x (nj+2) grid u[i][j] with the ring
+ * included, and an ni x nj array f.  i is the row (x, slow) and j the column (y, fast).
+ * Rectangular grids and a parity offset exist only so that tests can cut a window out
+ * of a large grid: a point (i, j) of the window is red when (i + j + parity) is even.
+ */
+#include <math.h>
+#include <stddef.h>
+
+#define U(i, j) u[(size_t)(i) * (size_t)(nj + 2) + (size_t)(j)]
+#define F(i, j) f[(size_t)((i) - 1) * (size_t)nj + (size_t)((j) - 1)]
+
+/* One colour of Eq. (1): every interior point whose colour is `colour` (0 red, 1 black). */
+static void half_sweep_f64(int ni, int nj, double h2, const double *f, double *u,
+                           int parity, int colour)
+{
+    for (int i = 1; i <= ni; ++i) {
+        for (int j = 1; j <= nj; ++j) {
+            if (((i + j + parity) & 1) != colour)
+                continue;
+            double s = h2 * F(i, j);
+            s = s + U(i - 1, j);
+            s = s + U(i + 1, j);
+            s = s + U(i, j - 1);
+            s = s + U(i, j + 1);
+            U(i, j) = s * 0.25;
+        }
+    }
+}
+
+/* nsweeps red+black sweeps in float64 (Section 2, Eq. (1); Algorithm 1's sweep order). */
+void ref_sweeps_f64(int ni, int nj, double h2, const double *f, double *u, long nsweeps,
+                    int parity)
+{
+    for (long it = 0; it < nsweeps; ++it) {
+        half_sweep_f64(ni, nj, h2, f, u, parity, 0);
+        half_sweep_f64(ni, nj, h2, f, u, parity, 1);
+    }
+}
+
+/* Single half-sweep, exported for tests of the colour phases. */
+void ref_half_sweep_f64(int ni, int nj, double h2, const double *f, double *u, int parity,
+                        int colour)
+{
+    half_sweep_f64(ni, nj, h2, f, u, parity, colour);
+}
+
+/* The same iteration carried out in binary32 (the mixed-precision inner solver). */
+void ref_sweeps_f32(int ni, int nj, float h2, const float *f, float *u, long nsweeps,
+                    int parity)
+{
+    for (long it = 0; it < nsweeps; ++it) {
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int i = 1; i <= ni; ++i) {
+                for (int j = 1; j <= nj; ++j) {
+                    if (((i + j + parity) & 1) != colour)
+                        continue;
+                    float s = h2 * F(i, j);
+                    s = s + U(i - 1, j);
+                    s = s + U(i + 1, j);
+                    s = s + U(i, j - 1);
+                    s = s + U(i, j + 1);
+                    U(i, j) = s * 0.25f;
+                }
+            }
+        }
+    }
+}
+
+/*
+ * Scaled residual of the discrete system A u = b, A = (4 I - neighbours) / h^2 on the
+ * interior, b = f plus the ring values / h^2 (Eq. (1) moved to one side):
+ *
+ *   rt_ij  = (((h^2 f_ij + u_{i-1,j}) + u_{i+1,j}) + u_{i,j-1}) + u_{i,j+1} - 4 u_ij
+ *          = h^2 (b - A u)_ij
+ *   hb_ij  = h^2 f_ij + the neighbours of (i, j) that lie on the ring, in the same order
+ *          = h^2 b_ij
+ *
+ * sums of squares accumulate in plain i-major order.  Writes sum rt^2 and sum hb^2 and
+ * returns rho = sqrt(sum rt^2) / sqrt(sum hb^2), or sqrt(sum rt^2) when b = 0.
+ */
+double ref_residual_f64(int ni, int nj, double h2, const double *f, const double *u,
+                        double *sum_r2, double *sum_b2)
+{
+    double r2 = 0.0, b2 = 0.0;
+    for (int i = 1; i <= ni; ++i) {
+        for (int j = 1; j <= nj; ++j) {
+            double hf = h2 * F(i, j);
+            double s = hf;
+            s = s + U(i - 1, j);
+            s = s + U(i + 1, j);
+            s = s + U(i, j - 1);
+            s = s + U(i, j + 1);
+            double r = s - 4.0 * U(i, j);
+            r2 = r2 + r * r;
+            double b = hf;
+            if (i == 1)  b = b + U(i - 1, j);
+            if (i == ni) b = b + U(i + 1, j);
+            if (j == 1)  b = b + U(i, j - 1);
+            if (j == nj) b = b + U(i, j + 1);
+            b2 = b2 + b * b;
+        }
+    }
+    if (sum_r2) *sum_r2 = r2;
+    if (sum_b2) *sum_b2 = b2;
+    return b2 > 0.0 ? sqrt(r2) / sqrt(b2) : sqrt(r2);
+}
+
+/* Pointwise scaled residual rt (ni x nj), for tests of the residual's structure. */
+void ref_residual_field_f64(int ni, int nj, double h2, const double *f, const double *u,
+                            double *r)
+{
+    for (int i = 1; i <= ni; ++i) {
+        for (int j = 1; j <= nj; ++j) {
+            double s = h2 * F(i, j);
+            s = s + U(i - 1, j);
+            s = s + U(i + 1, j);
+            s = s + U(i, j - 1);
+            s = s + U(i, j + 1);
+            r[(size_t)(i - 1) * (size_t)nj + (size_t)(j - 1)] = s - 4.0 * U(i, j);
+        }
+    }
+}
+
+/*
+ * Solve to a relative residual: check rho every `check_every` sweeps (and before the
+ * first sweep), stop at rho <= tol or after max_sweeps.  Returns the sweeps done and
+ * writes the last rho.  The paper fixes the iteration count instead (Section 4); the
+ * stopping rule is the library's convergence control, stated here in its plain form.
+ */
+long ref_solve_f64(int ni, int nj, double h2, const double *f, double *u, double tol,
+                   int check_every, long max_sweeps, double *rho_out)
+{
+    long done = 0;
+    double rho = ref_residual_f64(ni, nj, h2, f, u, NULL, NULL);
+    while (!(rho <= tol) && done < max_sweeps && isfinite(rho)) {
+        long k = check_every;
+        if (k > max_sweeps - done) k = max_sweeps - done;
+        ref_sweeps_f64(ni, nj, h2, f, u, k, 0);
+        done += k;
+        rho = ref_residual_f64(ni, nj, h2, f, u, NULL, NULL);
+    }
+    if (rho_out) *rho_out = rho;
+    return done;
+}
