@@ -1,0 +1,359 @@
+"""Benchmark: plain FP64 red-black Gauss-Seidel on a 16384 x 16384 interior.
+
+One step is one pass of the whole solver path over one synthetic problem, through the
+C ABI: rbgs_create (stage the natural-layout f and u0, split them into colours, scale
+h^2 f, reduce ||h^2 b||), rbgs_sweep(200) (400 half-sweep launches, red then black),
+rbgs_residual (the residual-norm reduction), rbgs_get_solution (back to the natural
+layout) and rbgs_destroy.  Problem: -Lap u = f, zero Dirichlet ring, f ~ U(-1, 1)
+i.i.d. from counter stream 1, u0 = 0, h = 1/16385.
+
+`value` is whole-job GLUP/s (lattice-site updates, N^2 per sweep) with the inputs
+resident in device memory; `e2e` is the same step with the inputs and the solution in
+pinned host memory (copies inside the timed region).  With N > 1 processes (torchrun)
+every rank solves its own replica (the single-grid path does not shard here) and the
+value is the sum over ranks over the slowest rank's time.
+
+--impl reference times the oracle (plain single-threaded C) on the host, one sweep of
+the same grid per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUP/s + HBM GB/s vs ~8 TB/s; time-to-residual 1e-8, plain vs chosen form"
+UNIT = "GLUP/s"
+BYTES_PER_LUP = 24  # FP64: read h2f and the other colour's value, write the own value
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "half_sweep_f64_n16384.md")
+KERNEL_SOURCES = ["paper_2607_01735_gb300/csrc/sweep.cu", "paper_2607_01735_gb300/csrc/sweep_impl.cuh",
+                  "paper_2607_01735_gb300/csrc/fp64.cuh"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--sweeps", type=int, default=200)
+    p.add_argument("--emulate", type=int, default=-1, help="FP64 add split (-1: library default)")
+    p.add_argument("--tile-rows", type=int, default=0)
+    p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one launch per colour, 2 temporal")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(n, sweeps):
+    return (f"plain RBGS FP64, {n}x{n} interior, zero Dirichlet ring, f~U(-1,1) seed 1, u0=0, "
+            f"{sweeps} red+black sweeps + residual norm")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(emulate):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches this kernel."""
+    try:
+        with open(PROFILE_SUMMARY) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    if str(vals.get("fp64_emulate")) != str(emulate):
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and self.uuid not in parts[1]:
+                    continue
+                try:
+                    sm.append(float(parts[2]))
+                    smax.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[6:10]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_rate(n, stream=1, target_s=10.0):
+    """Oracle GLUP/s on the host: sweeps of the same n x n problem, ~target_s of work."""
+    import numpy as np
+
+    import oracle
+    import synth
+    oracle.build()
+    f = synth.uniform_pm1_grid(n, stream).numpy()
+    u = np.zeros((n + 2, n + 2))
+    h2 = synth.h_squared(n)
+    t0 = time.perf_counter()
+    oracle.sweeps(u, f, h2, 1)
+    t1 = time.perf_counter()
+    done, elapsed = 1, t1 - t0
+    more = max(0, min(50, int(target_s / max(elapsed, 1e-9)) - 1))
+    if more:
+        t0 = time.perf_counter()
+        oracle.sweeps(u, f, h2, more)
+        elapsed += time.perf_counter() - t0
+        done += more
+    return {"value": n * n * done / elapsed / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} sweep(s) of the {n}x{n} grid (plain single-threaded C, -O2 "
+                      f"-ffp-contract=off), {elapsed:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import synth
+    oracle.build()
+    n = args.n
+    f = synth.uniform_pm1_grid(n, 1).numpy()
+    u = np.zeros((n + 2, n + 2))
+    h2 = synth.h_squared(n)
+    for _ in range(args.warmup):
+        oracle.sweeps(u, f, h2, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sweeps(u, f, h2, 1)
+        times.append(time.perf_counter() - t0)
+    t = sum(times)
+    value = n * n * args.steps / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload(n, args.sweeps), "n": n,
+                       "reference_step": "one sweep of the same grid by the oracle (the step is "
+                                         "bounded; the GPU arm's step is the full sweep count)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed sweep(s) of the {n}x{n} grid, one per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_2607_01735_gb300 as rb
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    n, sweeps = args.n, args.sweeps
+    h2 = synth.h_squared(n)
+    f = synth.uniform_pm1_grid(n, 1, device=dev)
+    u0 = torch.zeros(n + 2, n + 2, dtype=torch.float64, device=dev)
+    out = torch.empty_like(u0)
+    opts = rb.default_opts(fp64_emulate=args.emulate, tile_rows=args.tile_rows, kernel=args.kernel)
+    lib = rb.load_library()
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize(dev)
+
+    sweep_events = []
+
+    def step(fi, ui, uo, record=False):
+        ctx = rb.rbgs_create(n, h2, fi, ui, opts, stream=stream.cuda_stream)
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        rb.rbgs_sweep(ctx, sweeps)
+        if record:
+            e1.record(stream)
+            sweep_events.append((e0, e1))
+        rho = rb.rbgs_residual(ctx)
+        rb.rbgs_get_solution(ctx, uo)
+        rb.rbgs_destroy(ctx)
+        return rho
+
+    launches_per_step = 4 + 2 * sweeps + 3 + 1  # pack f, pack u, ||b|| (2), sweeps, residual (3), unpack
+
+    for _ in range(args.warmup):
+        step(f, u0, out)
+    barrier()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    with ClockSampler(str(uuid) if uuid else None) as clocks:
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            rho = step(f, u0, out, record=True)
+        t1.record(stream)
+        barrier()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    if world > 1:
+        tt = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    lups = float(n) * n * sweeps * args.steps * world
+    value = lups / elapsed / 1e9
+    sweep_s = sum(a.elapsed_time(b) for a, b in sweep_events) / 1e3
+    launch_s = sweep_s / (2 * sweeps * args.steps)
+    alg_bytes_launch = BYTES_PER_LUP * (n * n / 2.0)
+    achieved = alg_bytes_launch / launch_s / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+    emulate_used = args.emulate
+    traffic = profiled_traffic(emulate_used)
+
+    e2e = None
+    if not args.no_e2e:
+        fh = f.cpu().pin_memory()
+        uh = u0.cpu().pin_memory()
+        oh = torch.empty(n + 2, n + 2, dtype=torch.float64).pin_memory()
+        step(fh, uh, oh)  # warm the host path once
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(fh, uh, oh)
+        e1.record(stream)
+        barrier()
+        et = e0.elapsed_time(e1) / 1e3
+        if world > 1:
+            tt = torch.tensor([et], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            et = float(tt.item())
+        e2e = {"value": lups / et / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 8 * (n * n + (n + 2) * (n + 2)),
+               "d2h_bytes_per_step": 8 * (n + 2) * (n + 2) + 8,
+               "ms_per_step": 1e3 * et / args.steps}
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_oracle_rate(n)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 f ~ U(-1,1))",
+            "config": {"workload": workload(n, sweeps), "n": n, "sweeps": sweeps,
+                       "kernel": "one launch per colour" if args.kernel in (0, 1) else "temporal",
+                       "fp64_emulate": emulate_used, "tile_rows": args.tile_rows or "auto",
+                       "l2": "inputs larger than L2 (4 colour arrays of 1.08 GB each)",
+                       "parallelism": f"replicas x{world}"},
+            "hbm_gbs_algorithmic": BYTES_PER_LUP * lups / elapsed / 1e9,
+            "final_rho": rho,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "half_sweep_f64", "peak_source": peak_src,
+                         "launch_ms": 1e3 * launch_s,
+                         "algorithmic_bytes_per_launch": alg_bytes_launch},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,146 @@
+/*
+ * rbgs.h -- C ABI of librbgs.so: red-black Gauss-Seidel (RBGS) for the 2D Poisson
+ * equation on GB300 (sm_103a).
+ *
+ * The method (Section 2 of "Exploiting Task-Based Parallelism for the Red-Black
+ * Gauss-Seidel Method on 2D Grids", Long, Ramirez-Hidalgo, Frommer, Pleiter):
+ *   -Lap u = f on the unit square, u = g on the boundary (the paper writes Lap u = f;
+ *   this is the same problem with f -> -f), uniform grid h = 1/(N+1), and the 5-point
+ *   update of Eq. (1),
+ *       u_ij <- (h^2 f_ij + u_{i-1,j} + u_{i+1,j} + u_{i,j-1} + u_{i,j+1}) / 4,
+ *   applied first to every red point (i + j even) and then to every black point
+ *   (i + j odd); one red+black pair is one sweep (Algorithms 1 and 2).
+ *
+ * Arithmetic: every update is evaluated as (((h2*f + N) + S) + W) + E, times 0.25, with
+ * each operation correctly rounded and no fused multiply-add, so the FP64 path gives
+ * the same bits as a plain sequential C loop in that order.
+ *
+ * Grids, all row-major, i = row (x, slow), j = column (y, fast):
+ *   f      N x N interior values (f_ij at index (i-1)*N + (j-1)), float64
+ *   u      (N+2) x (N+2) including the Dirichlet ring (u_ij at index i*(N+2) + j);
+ *          the ring holds g and stays fixed, the interior is the iterate
+ * Pointers may address device memory or host memory (pageable or pinned); the library
+ * copies through the CUDA runtime with unified addressing.  The caller keeps ownership
+ * of everything it passes; the library owns the buffers inside a context.
+ *
+ * Errors: every call returns an rbgs_status; nothing is thrown across the ABI.  On a
+ * non-OK status rbgs_last_error() returns a message for the calling thread.  CUDA
+ * errors from a failed launch leave the context usable only for rbgs_destroy.
+ * Work is ordered on the stream given at creation (NULL = the legacy default stream);
+ * calls that return a host scalar synchronise that stream.
+ */
+#ifndef RBGS_H
+#define RBGS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbgs_ctx *rbgs_t;
+
+typedef enum {
+    RBGS_OK = 0,
+    RBGS_EINVAL = 1,      /* bad argument: null pointer, n < 1, h2 <= 0, bad option     */
+    RBGS_ENOMEM = 2,      /* device or pinned host allocation failed                     */
+    RBGS_ECUDA = 3,       /* a CUDA runtime/driver call failed                           */
+    RBGS_ENOTCONV = 4,    /* rbgs_solve reached max_sweeps; the iterate is kept          */
+    RBGS_ENONFINITE = 5,  /* the residual became NaN or Inf                              */
+    RBGS_ETIMEOUT = 6     /* a bounded device-side wait gave up (batched solver)         */
+} rbgs_status;
+
+typedef enum {
+    RBGS_FP64 = 0,        /* plain FP64 sweeps                                            */
+    RBGS_FP32_REFINE = 1  /* FP32 sweeps on the defect equation + FP64 residual/correction */
+} rbgs_precision;
+
+typedef enum {
+    RBGS_KERNEL_AUTO = 0,
+    RBGS_KERNEL_COLOUR = 1,   /* one launch per colour (half-sweep kernels)               */
+    RBGS_KERNEL_TEMPORAL = 2  /* several sweeps per shared-memory tile, halo recompute      */
+} rbgs_kernel;
+
+typedef struct {
+    int precision;     /* rbgs_precision                                                  */
+    int kernel;        /* rbgs_kernel                                                     */
+    int check_every;   /* sweeps between residual checks in rbgs_solve (0: 100)            */
+    long max_sweeps;   /* rbgs_solve gives up after this many sweeps (0: 1e9)              */
+    int tblock_k;      /* sweeps per tile pass for RBGS_KERNEL_TEMPORAL (0: automatic)     */
+    int tile_rows;     /* rows per thread block (0: automatic)                             */
+    int fp64_emulate;  /* FP64 adds issued on the integer pipe per 8 (-1: automatic)       */
+    int inner_sweeps;  /* FP32 sweeps per defect correction for RBGS_FP32_REFINE (0: auto) */
+} rbgs_opts;
+
+/* Fills *opts with the defaults (all automatic). */
+void rbgs_default_opts(rbgs_opts *opts);
+
+/*
+ * Creates a solver for one N x N problem (Section 2: h = 1/(N+1), the caller passes
+ * h2 = h*h as it wants it rounded).  f: N*N values; u_init: (N+2)^2 values with the
+ * Dirichlet ring and the initial guess.  opts may be NULL (defaults).  The stream is a
+ * cudaStream_t (NULL: legacy default stream).  On success *out owns device buffers of
+ * about 4 (N+2)^2 doubles (plus FP32 copies for RBGS_FP32_REFINE).
+ */
+rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
+                        const rbgs_opts *opts, void *cuda_stream, rbgs_t *out);
+
+/* nsweeps red+black sweeps of Eq. (1) (Algorithm 1's iteration; nsweeps >= 0). Async. */
+rbgs_status rbgs_sweep(rbgs_t ctx, long nsweeps);
+
+/*
+ * Relative residual rho = ||b - A u||_2 / ||b||_2 of the current iterate, with
+ * A = (4 I - neighbours)/h^2 and b = f plus the ring terms / h^2 (the linear system of
+ * Eq. (1)); rho = ||b - A u||_2 * h^2 when b = 0.  Synchronises the stream.
+ * Returns RBGS_ENONFINITE (and writes rho) when rho is NaN or Inf.
+ */
+rbgs_status rbgs_residual(rbgs_t ctx, double *rel);
+
+/*
+ * Sweeps until rho <= tol, evaluating rho before the first sweep and then every
+ * check_every sweeps.  *sweeps_done gets the sweeps performed, *rel the last rho
+ * (either may be NULL).  RBGS_ENOTCONV after max_sweeps, RBGS_ENONFINITE on NaN/Inf.
+ */
+rbgs_status rbgs_solve(rbgs_t ctx, double tol, long *sweeps_done, double *rel);
+
+/* Copies the current iterate, ring included, into u_out ((N+2)^2 values). */
+rbgs_status rbgs_get_solution(rbgs_t ctx, double *u_out);
+
+/* Replaces the iterate and the ring by u_in ((N+2)^2 values), e.g. to resume a run. */
+rbgs_status rbgs_set_solution(rbgs_t ctx, const double *u_in);
+
+/* Problem n of a batch: interior size, h^2, f (N*N) and u_init ((N+2)^2). */
+typedef struct {
+    int n;
+    double h2;
+    const double *f;
+    const double *u_init;
+} rbgs_problem;
+
+/* Per-problem outcome of rbgs_solve_batched. */
+typedef struct {
+    int status;          /* rbgs_status of this problem                                   */
+    long sweeps;         /* sweeps performed                                              */
+    double rel;          /* final relative residual                                       */
+    double latency_ms;   /* device time from the batch start to this problem's completion  */
+} rbgs_result;
+
+/*
+ * Solves nprob independent problems of uneven sizes to rho <= tol each, in one
+ * persistent launch.  u_out[p] receives problem p's solution ((N_p+2)^2 values); res[p]
+ * its outcome.  Returns RBGS_OK when every problem converged, else the first failing
+ * status.  Synchronises the stream.
+ */
+rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, double tol,
+                               const rbgs_opts *opts, void *cuda_stream, double **u_out,
+                               rbgs_result *res);
+
+/* Frees the context (NULL is ignored). Synchronises its stream first. */
+void rbgs_destroy(rbgs_t ctx);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char *rbgs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBGS_H */

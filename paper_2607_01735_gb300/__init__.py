@@ -1,0 +1,245 @@
+"""GB300-native red-black Gauss-Seidel (RBGS) for the 2D Poisson equation.
+
+A thin ctypes binding over ``librbgs.so`` (C ABI in ``include/rbgs.h``).  The names
+match the C entry points; this module only marshals arguments (tensors -> pointers,
+status codes -> exceptions).  Every step of the solve runs in the library's CUDA
+kernels; there is no CPU fallback: importing works without a GPU, but any call that
+needs the library raises if ``librbgs.so`` has not been built
+(``python -m paper_2607_01735_gb300.build``).
+
+Arrays: ``f`` is N x N and ``u`` is (N+2) x (N+2) (Dirichlet ring included), float64,
+C-contiguous; torch tensors (CPU or CUDA) or numpy arrays.  h2 = h*h with h = 1/(N+1)
+(Section 2 of the paper).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librbgs.so")
+
+RBGS_OK, RBGS_EINVAL, RBGS_ENOMEM, RBGS_ECUDA, RBGS_ENOTCONV, RBGS_ENONFINITE, RBGS_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "RBGS_OK", 1: "RBGS_EINVAL", 2: "RBGS_ENOMEM", 3: "RBGS_ECUDA",
+                4: "RBGS_ENOTCONV", 5: "RBGS_ENONFINITE", 6: "RBGS_ETIMEOUT"}
+RBGS_FP64, RBGS_FP32_REFINE = 0, 1
+RBGS_KERNEL_AUTO, RBGS_KERNEL_COLOUR, RBGS_KERNEL_TEMPORAL = 0, 1, 2
+
+# Every symbol include/rbgs.h declares.
+EXPORTED = ("rbgs_default_opts", "rbgs_create", "rbgs_sweep", "rbgs_residual", "rbgs_solve",
+            "rbgs_get_solution", "rbgs_set_solution", "rbgs_solve_batched", "rbgs_destroy",
+            "rbgs_last_error")
+
+
+class RbgsError(RuntimeError):
+    """A non-OK rbgs_status, with the library's message."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("max_sweeps", ctypes.c_long),
+                ("tblock_k", ctypes.c_int), ("tile_rows", ctypes.c_int),
+                ("fp64_emulate", ctypes.c_int), ("inner_sweeps", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("h2", ctypes.c_double),
+                ("f", ctypes.c_void_p), ("u_init", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("sweeps", ctypes.c_long),
+                ("rel", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load librbgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"librbgs.so not found at {path}: build it with "
+                           "`python -m paper_2607_01735_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, c_int, c_long, c_double = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
+    lib.rbgs_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.rbgs_default_opts.restype = None
+    lib.rbgs_create.argtypes = [c_int, c_double, vp, vp, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.rbgs_create.restype = c_int
+    lib.rbgs_sweep.argtypes = [vp, c_long]
+    lib.rbgs_sweep.restype = c_int
+    lib.rbgs_residual.argtypes = [vp, ctypes.POINTER(c_double)]
+    lib.rbgs_residual.restype = c_int
+    lib.rbgs_solve.argtypes = [vp, c_double, ctypes.POINTER(c_long), ctypes.POINTER(c_double)]
+    lib.rbgs_solve.restype = c_int
+    lib.rbgs_get_solution.argtypes = [vp, vp]
+    lib.rbgs_get_solution.restype = c_int
+    lib.rbgs_set_solution.argtypes = [vp, vp]
+    lib.rbgs_set_solution.restype = c_int
+    lib.rbgs_solve_batched.argtypes = [c_int, ctypes.POINTER(Problem), c_double, ctypes.POINTER(Opts),
+                                       vp, ctypes.POINTER(vp), ctypes.POINTER(Result)]
+    lib.rbgs_solve_batched.restype = c_int
+    lib.rbgs_destroy.argtypes = [vp]
+    lib.rbgs_destroy.restype = None
+    lib.rbgs_last_error.argtypes = []
+    lib.rbgs_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def rbgs_last_error() -> str:
+    return load_library().rbgs_last_error().decode()
+
+
+def _check(status: int, allowed=(RBGS_OK,)) -> int:
+    if status not in allowed:
+        raise RbgsError(status, rbgs_last_error())
+    return status
+
+
+def _ptr(a, dtype_name: str = "float64") -> int:
+    """Address of a contiguous float64 torch tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype_name) or not a.flags.c_contiguous:
+            raise TypeError(f"expected a C-contiguous {dtype_name} numpy array")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != getattr(torch, dtype_name) or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {dtype_name} tensor")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)!r}")
+
+
+def _stream_of(*arrays, stream=None) -> int | None:
+    if stream is not None:
+        return int(stream)
+    import torch
+    for a in arrays:
+        if isinstance(a, torch.Tensor) and a.is_cuda:
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load_library().rbgs_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def rbgs_create(n: int, h2: float, f, u_init, opts: Opts | None = None, stream=None) -> int:
+    """rbgs_create: returns the context handle (an integer)."""
+    lib = load_library()
+    h = ctypes.c_void_p()
+    s = _stream_of(f, u_init, stream=stream)
+    _check(lib.rbgs_create(int(n), float(h2), _ptr(f), _ptr(u_init),
+                           ctypes.byref(opts) if opts is not None else None, s, ctypes.byref(h)))
+    return h.value
+
+
+def rbgs_sweep(ctx: int, nsweeps: int) -> None:
+    _check(load_library().rbgs_sweep(ctx, int(nsweeps)))
+
+
+def rbgs_residual(ctx: int) -> float:
+    rel = ctypes.c_double()
+    _check(load_library().rbgs_residual(ctx, ctypes.byref(rel)))
+    return rel.value
+
+
+def rbgs_solve(ctx: int, tol: float, allow_not_converged: bool = False) -> tuple[int, float, int]:
+    """rbgs_solve: returns (sweeps_done, rho, status)."""
+    done, rel = ctypes.c_long(), ctypes.c_double()
+    allowed = (RBGS_OK, RBGS_ENOTCONV) if allow_not_converged else (RBGS_OK,)
+    st = _check(load_library().rbgs_solve(ctx, float(tol), ctypes.byref(done), ctypes.byref(rel)), allowed)
+    return done.value, rel.value, st
+
+
+def rbgs_get_solution(ctx: int, u_out) -> None:
+    _check(load_library().rbgs_get_solution(ctx, _ptr(u_out)))
+
+
+def rbgs_set_solution(ctx: int, u_in) -> None:
+    _check(load_library().rbgs_set_solution(ctx, _ptr(u_in)))
+
+
+def rbgs_destroy(ctx: int) -> None:
+    if ctx:
+        load_library().rbgs_destroy(ctx)
+
+
+def rbgs_solve_batched(problems, tol: float, u_out: list, opts: Opts | None = None, stream=None,
+                       allow_failures: bool = False) -> list[dict]:
+    """problems: list of (n, h2, f, u_init); u_out: list of (n+2)^2 output arrays."""
+    lib = load_library()
+    k = len(problems)
+    arr = (Problem * max(k, 1))()
+    for p, (n, h2, f, u) in enumerate(problems):
+        arr[p] = Problem(int(n), float(h2), _ptr(f), _ptr(u))
+    outs = (ctypes.c_void_p * max(k, 1))(*[_ptr(u) for u in u_out])
+    res = (Result * max(k, 1))()
+    s = _stream_of(*(x for p in problems for x in p[2:]), stream=stream)
+    st = lib.rbgs_solve_batched(k, arr, float(tol), ctypes.byref(opts) if opts is not None else None,
+                                s, outs, res)
+    if not allow_failures:
+        _check(st)
+    return [{"status": r.status, "sweeps": r.sweeps, "rel": r.rel, "latency_ms": r.latency_ms}
+            for r in res[:k]]
+
+
+class Solver:
+    """Owning wrapper: ``with Solver(n, h2, f, u0) as s: s.sweep(10); s.residual()``."""
+
+    def __init__(self, n, h2, f, u_init, opts: Opts | None = None, stream=None, **kw):
+        if kw:
+            opts = opts or default_opts()
+            for key, v in kw.items():
+                setattr(opts, key, v)
+        self.n = n
+        self.ctx = rbgs_create(n, h2, f, u_init, opts, stream)
+
+    def sweep(self, nsweeps: int) -> None:
+        rbgs_sweep(self.ctx, nsweeps)
+
+    def residual(self) -> float:
+        return rbgs_residual(self.ctx)
+
+    def solve(self, tol: float, allow_not_converged: bool = False):
+        return rbgs_solve(self.ctx, tol, allow_not_converged)
+
+    def get_solution(self, u_out) -> None:
+        rbgs_get_solution(self.ctx, u_out)
+
+    def set_solution(self, u_in) -> None:
+        rbgs_set_solution(self.ctx, u_in)
+
+    def close(self) -> None:
+        if self.ctx:
+            rbgs_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

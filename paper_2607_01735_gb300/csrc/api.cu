@@ -1,0 +1,304 @@
+// C ABI entry points of librbgs (declared in include/rbgs.h): context life cycle,
+// layout staging, sweep scheduling (direct launches or a cached CUDA graph), residual
+// evaluation and the convergence loop.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "sweep_impl.cuh"
+
+namespace rbgs {
+
+namespace {
+thread_local char g_err[1024] = "";
+}
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+namespace {
+
+constexpr int kMaxN = 1 << 18;
+constexpr long kGraphSweeps = 32;    // sweeps per cached graph
+constexpr int kGraphMaxN = 2048;     // graphs pay off where launches dominate
+
+bool device_accessible(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device-readable natural-layout view of a caller buffer: the pointer itself when the
+// GPU can read it, else a copy in the context's staging buffer (stream-ordered).
+rbgs_status stage_in(rbgs_ctx *c, const double *src, size_t count, const double **view) {
+    if (device_accessible(src)) {
+        *view = src;
+        return RBGS_OK;
+    }
+    if (!c->staging) {
+        size_t nat = (size_t)c->g.rows * c->g.rows;
+        if (cudaMalloc(&c->staging, nat * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc of the %zu-byte staging buffer failed", nat * sizeof(double));
+            return RBGS_ENOMEM;
+        }
+    }
+    RBGS_CUDA(cudaMemcpyAsync(c->staging, src, count * sizeof(double), cudaMemcpyDefault, c->stream));
+    *view = c->staging;
+    return RBGS_OK;
+}
+
+rbgs_status load_problem(rbgs_ctx *c, const double *f, const double *u_init) {
+    const Geometry &g = c->g;
+    const double *view = nullptr;
+    rbgs_status st;
+    if (f) {
+        if ((st = stage_in(c, f, (size_t)g.n * g.n, &view)) != RBGS_OK) return st;
+        if ((st = launch_pack_f(g, c->h2, view, c->hf[0], c->hf[1], c->stream)) != RBGS_OK) return st;
+    }
+    if ((st = stage_in(c, u_init, (size_t)g.rows * g.rows, &view)) != RBGS_OK) return st;
+    if ((st = launch_pack_u(g, view, c->u[0], c->u[1], c->stream)) != RBGS_OK) return st;
+    // ||h^2 b||^2 depends on f and the ring
+    if ((st = launch_rhs_norm(c, c->stream)) != RBGS_OK) return st;
+    RBGS_CUDA(cudaMemcpyAsync(c->hsum + 1, c->dsum + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    RBGS_CUDA(cudaStreamSynchronize(c->stream));
+    c->den2 = c->hsum[1];
+    return RBGS_OK;
+}
+
+void free_ctx(rbgs_ctx *c) {
+    if (!c) return;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (int q = 0; q < 2; ++q) {
+        cudaFree(c->u[q]);
+        cudaFree(c->hf[q]);
+        cudaFree(c->d32[q]);
+        cudaFree(c->r32[q]);
+    }
+    cudaFree(c->staging);
+    cudaFree(c->partials);
+    cudaFree(c->dsum);
+    if (c->hsum) cudaFreeHost(c->hsum);
+    if (c->capture) cudaStreamDestroy(c->capture);
+    delete c;
+}
+
+rbgs_status enqueue_sweeps(rbgs_ctx *c, long nsweeps, cudaStream_t s) {
+    if (c->kernel == RBGS_KERNEL_TEMPORAL) return launch_temporal_sweeps(c, nsweeps, s);
+    return launch_sweeps_f64(c, nsweeps, s);
+}
+
+rbgs_status ensure_graph(rbgs_ctx *c) {
+    if (c->graph) return RBGS_OK;
+    cudaGraph_t graph = nullptr;
+    RBGS_CUDA(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+    rbgs_status st = enqueue_sweeps(c, kGraphSweeps, c->capture);
+    cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
+    if (st != RBGS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        set_error("graph capture failed: %s", cudaGetErrorString(e));
+        return RBGS_ECUDA;
+    }
+    e = cudaGraphInstantiate(&c->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+        return RBGS_ECUDA;
+    }
+    c->graph_sweeps = kGraphSweeps;
+    return RBGS_OK;
+}
+
+}  // namespace
+}  // namespace rbgs
+
+using namespace rbgs;
+
+extern "C" {
+
+void rbgs_default_opts(rbgs_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = RBGS_FP64;
+    o->kernel = RBGS_KERNEL_AUTO;
+    o->check_every = 100;
+    o->max_sweeps = 1000000000L;
+    o->fp64_emulate = -1;
+}
+
+const char *rbgs_last_error(void) { return g_err; }
+
+rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
+                        const rbgs_opts *opts, void *cuda_stream, rbgs_t *out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return RBGS_EINVAL; }
+    *out = nullptr;
+    if (n < 1 || n > kMaxN) { set_error("n = %d outside 1..%d", n, kMaxN); return RBGS_EINVAL; }
+    if (!(h2 > 0.0) || !std::isfinite(h2)) { set_error("h2 must be finite and > 0"); return RBGS_EINVAL; }
+    if (!f || !u_init) { set_error("f and u_init must not be NULL"); return RBGS_EINVAL; }
+    rbgs_opts o;
+    rbgs_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.check_every <= 0) o.check_every = 100;
+    if (o.max_sweeps <= 0) o.max_sweeps = 1000000000L;
+    if (o.precision != RBGS_FP64 && o.precision != RBGS_FP32_REFINE) {
+        set_error("unknown precision %d", o.precision); return RBGS_EINVAL;
+    }
+    if (o.kernel < RBGS_KERNEL_AUTO || o.kernel > RBGS_KERNEL_TEMPORAL) {
+        set_error("unknown kernel %d", o.kernel); return RBGS_EINVAL;
+    }
+    if (o.fp64_emulate != -1 && !emulation_split_supported(o.fp64_emulate)) {
+        set_error("unsupported fp64_emulate %d", o.fp64_emulate); return RBGS_EINVAL;
+    }
+    if (o.tile_rows < 0 || o.tblock_k < 0 || o.inner_sweeps < 0) {
+        set_error("negative tile_rows / tblock_k / inner_sweeps"); return RBGS_EINVAL;
+    }
+
+    rbgs_ctx *c = new (std::nothrow) rbgs_ctx();
+    if (!c) { set_error("out of host memory"); return RBGS_ENOMEM; }
+    c->g = make_geometry(n);
+    c->h2 = h2;
+    c->opts = o;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->kernel = o.kernel == RBGS_KERNEL_AUTO ? RBGS_KERNEL_COLOUR : o.kernel;
+    c->emulate = o.fp64_emulate == -1 ? 0x00 : o.fp64_emulate;
+    c->tile_rows = o.tile_rows ? o.tile_rows : 32;
+    c->tblock_k = o.tblock_k;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        set_error("no CUDA device");
+        return RBGS_ECUDA;
+    }
+    const size_t bytes = c->g.colour_elems() * sizeof(double);
+    bool ok = true;
+    for (int q = 0; q < 2 && ok; ++q) {
+        ok = cudaMalloc(&c->u[q], bytes) == cudaSuccess && cudaMalloc(&c->hf[q], bytes) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&c->partials, kMaxPartials * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->dsum, 4 * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&c->hsum, 4 * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_ctx(c);
+        set_error("allocation of %zu bytes of solver state failed", 4 * bytes);
+        return RBGS_ENOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        set_error("stream creation failed");
+        return RBGS_ECUDA;
+    }
+    rbgs_status st = load_problem(c, f, u_init);
+    if (st != RBGS_OK) {
+        free_ctx(c);
+        return st;
+    }
+    *out = c;
+    return RBGS_OK;
+}
+
+rbgs_status rbgs_sweep(rbgs_t c, long nsweeps) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return RBGS_EINVAL; }
+    if (nsweeps < 0) { set_error("nsweeps < 0"); return RBGS_EINVAL; }
+    if (c->g.n <= kGraphMaxN && nsweeps >= kGraphSweeps) {
+        rbgs_status st = ensure_graph(c);
+        if (st != RBGS_OK) return st;
+        while (nsweeps >= c->graph_sweeps) {
+            RBGS_CUDA(cudaGraphLaunch(c->graph, c->stream));
+            nsweeps -= c->graph_sweeps;
+        }
+    }
+    return enqueue_sweeps(c, nsweeps, c->stream);
+}
+
+rbgs_status rbgs_residual(rbgs_t c, double *rel) {
+    clear_error();
+    if (!c || !rel) { set_error("ctx and rel must not be NULL"); return RBGS_EINVAL; }
+    rbgs_status st = launch_residual_sum(c, c->stream);
+    if (st != RBGS_OK) return st;
+    RBGS_CUDA(cudaMemcpyAsync(c->hsum, c->dsum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    RBGS_CUDA(cudaStreamSynchronize(c->stream));
+    const double r2 = c->hsum[0];
+    *rel = c->den2 > 0.0 ? std::sqrt(r2) / std::sqrt(c->den2) : std::sqrt(r2);
+    if (!std::isfinite(*rel)) {
+        set_error("residual is not finite");
+        return RBGS_ENONFINITE;
+    }
+    return RBGS_OK;
+}
+
+rbgs_status rbgs_solve(rbgs_t c, double tol, long *sweeps_done, double *rel) {
+    clear_error();
+    if (!c) { set_error("ctx is NULL"); return RBGS_EINVAL; }
+    if (!(tol >= 0.0)) { set_error("tol must be >= 0"); return RBGS_EINVAL; }
+    long done = 0;
+    double rho = 0.0;
+    rbgs_status st = rbgs_residual(c, &rho);
+    while (st == RBGS_OK && !(rho <= tol) && done < c->opts.max_sweeps) {
+        long k = c->opts.check_every;
+        if (k > c->opts.max_sweeps - done) k = c->opts.max_sweeps - done;
+        if ((st = rbgs_sweep(c, k)) != RBGS_OK) break;
+        done += k;
+        st = rbgs_residual(c, &rho);
+    }
+    if (sweeps_done) *sweeps_done = done;
+    if (rel) *rel = rho;
+    if (st == RBGS_OK && !(rho <= tol)) {
+        set_error("not converged after %ld sweeps (rho = %.3e)", done, rho);
+        st = RBGS_ENOTCONV;
+    }
+    return st;
+}
+
+rbgs_status rbgs_get_solution(rbgs_t c, double *u_out) {
+    clear_error();
+    if (!c || !u_out) { set_error("ctx and u_out must not be NULL"); return RBGS_EINVAL; }
+    const size_t count = (size_t)c->g.rows * c->g.rows;
+    if (device_accessible(u_out)) {
+        return launch_unpack_u(c->g, c->u[0], c->u[1], u_out, c->stream);
+    }
+    if (!c->staging) {
+        if (cudaMalloc(&c->staging, count * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("staging allocation failed");
+            return RBGS_ENOMEM;
+        }
+    }
+    rbgs_status st = launch_unpack_u(c->g, c->u[0], c->u[1], c->staging, c->stream);
+    if (st != RBGS_OK) return st;
+    RBGS_CUDA(cudaMemcpyAsync(u_out, c->staging, count * sizeof(double), cudaMemcpyDefault, c->stream));
+    RBGS_CUDA(cudaStreamSynchronize(c->stream));
+    return RBGS_OK;
+}
+
+rbgs_status rbgs_set_solution(rbgs_t c, const double *u_in) {
+    clear_error();
+    if (!c || !u_in) { set_error("ctx and u_in must not be NULL"); return RBGS_EINVAL; }
+    return load_problem(c, nullptr, u_in);
+}
+
+void rbgs_destroy(rbgs_t c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+}  // extern "C"

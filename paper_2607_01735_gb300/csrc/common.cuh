@@ -1,0 +1,115 @@
+// Shared definitions of librbgs: the solver context, the colour-split layout and error
+// plumbing.  Internal to the library (the public ABI is include/rbgs.h).
+//
+// Colour-split layout (the red/black split storage of Section 2.1 of the paper, with
+// padded rows): colour c (0 red, 1 black) of grid row i, 0 <= i <= N+1, is a row of W
+// values; element k holds the natural point j = 2k + ((i + c) & 1).  A red point and its
+// north/south neighbours share k; its west/east neighbours sit at k-1/k when the row's
+// red offset (i & 1) is 0 and at k/k+1 when it is 1.  W = ceil((N+2)/2) rounded up to a
+// multiple of 32 values (256 bytes), so every row starts on a 256-byte boundary and a
+// half-sweep reads and writes each value of a colour once.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/rbgs.h"
+
+namespace rbgs {
+
+// message for rbgs_last_error(); thread-local
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define RBGS_CUDA(call)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ::rbgs::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                              __FILE__, __LINE__);                                       \
+            return RBGS_ECUDA;                                                           \
+        }                                                                                \
+    } while (0)
+
+#define RBGS_LAUNCH_CHECK()                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = cudaGetLastError();                                             \
+        if (e_ != cudaSuccess) {                                                         \
+            ::rbgs::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_), \
+                              __FILE__, __LINE__);                                       \
+            return RBGS_ECUDA;                                                           \
+        }                                                                                \
+    } while (0)
+
+constexpr int kRowAlign = 32;  // values per row alignment unit (256 B of FP64)
+
+inline int colour_width(int n) {
+    int w = (n + 3) / 2;
+    return (w + kRowAlign - 1) / kRowAlign * kRowAlign;
+}
+
+// Geometry of one grid in the colour-split layout.
+struct Geometry {
+    int n;       // interior points per side
+    int W;       // values per colour row (padded)
+    int rows;    // n + 2
+    size_t colour_elems() const { return (size_t)rows * (size_t)W; }
+};
+
+inline Geometry make_geometry(int n) { return Geometry{n, colour_width(n), n + 2}; }
+
+// Residual reduction scratch: one partial sum per thread block.
+constexpr int kMaxPartials = 8192;
+
+struct Ctx;
+
+}  // namespace rbgs
+
+struct rbgs_ctx {
+    rbgs::Geometry g;
+    double h2;
+    rbgs_opts opts;
+    cudaStream_t stream;        // caller's stream (may be 0)
+    cudaStream_t capture;       // private stream used only to capture graphs
+    int device;
+    // FP64 iterate and scaled right-hand side h2*f, colour-split
+    double *u[2];
+    double *hf[2];
+    // FP32 copies for the mixed-precision inner solver (allocated on demand)
+    float *d32[2];
+    float *r32[2];
+    // natural-layout staging for host I/O (allocated on demand)
+    double *staging;
+    // reduction scratch and results
+    double *partials;
+    double *dsum;               // device: [0] sum r^2, [1] sum b^2, [2] max |r|
+    double *hsum;               // pinned host mirror
+    double den2;                // sum (h^2 b)^2, fixed by f and the ring
+    // cached graph of `graph_sweeps` sweeps
+    cudaGraphExec_t graph;
+    long graph_sweeps;
+    int kernel;                 // resolved rbgs_kernel
+    int emulate;                // resolved FP64 emulation split
+    int tile_rows;              // resolved rows per block
+    int tblock_k;               // resolved temporal depth
+};
+
+namespace rbgs {
+
+// launchers implemented in the .cu files; all enqueue on `s` and return a status
+rbgs_status launch_pack_u(const Geometry &g, const double *u_nat, double *red, double *black,
+                          cudaStream_t s);
+rbgs_status launch_pack_f(const Geometry &g, double h2, const double *f_nat, double *hf_red,
+                          double *hf_black, cudaStream_t s);
+rbgs_status launch_unpack_u(const Geometry &g, const double *red, const double *black,
+                            double *u_nat, cudaStream_t s);
+rbgs_status launch_half_sweep(const rbgs_ctx *c, int colour, cudaStream_t s);
+rbgs_status launch_sweeps_f64(const rbgs_ctx *c, long nsweeps, cudaStream_t s);
+rbgs_status launch_residual_sum(const rbgs_ctx *c, cudaStream_t s);   // -> dsum[0]
+rbgs_status launch_rhs_norm(const rbgs_ctx *c, cudaStream_t s);       // -> dsum[1]
+rbgs_status launch_temporal_sweeps(const rbgs_ctx *c, long nsweeps, cudaStream_t s);
+
+}  // namespace rbgs

@@ -1,0 +1,146 @@
+// Residual-norm reduction (the convergence test of the solver).
+//
+// For every interior point, rt = ((((h2f + N) + S) + W) + E) - 4 u equals h^2 (b - A u)
+// for the linear system of Eq. (1) with the ring folded into b.  The kernels walk the
+// colour-split grid the same way the half-sweeps do (strip of rows per block, other
+// colour's rows i-1, i, i+1 in registers), square each rt and reduce: warp shuffle,
+// then the block, then one partial per block; a single-block kernel adds the partials
+// in a fixed order.  The result is the same on every run.
+//
+// ||h^2 b|| depends only on f and the ring; it is reduced once per problem by
+// rhs_norm_kernel (h2f plus the ring neighbours of each boundary-adjacent point).
+#include "common.cuh"
+#include "sweep_impl.cuh"
+
+namespace rbgs {
+namespace {
+
+constexpr int kFinalThreads = 1024;
+
+template <int COLOUR>
+__global__ void __launch_bounds__(kSweepThreads)
+residual_colour_kernel(const double *__restrict__ self, const double *__restrict__ other,
+                       const double *__restrict__ hf, int n, int W, int kact,
+                       int rows_per_block, double *__restrict__ partials) {
+    __shared__ double red_smem[kSweepThreads / 32];
+    const int lane = threadIdx.x & 31;
+    const int k0 = 2 * (blockIdx.x * kSweepThreads + threadIdx.x);
+    const bool act = k0 < kact;
+    const int i0 = 1 + blockIdx.y * rows_per_block;
+    const int i1 = min(n, i0 + rows_per_block - 1);
+    const double2 zero = make_double2(0.0, 0.0);
+    double acc = 0.0;
+    if (i0 <= n) {
+        double2 up = act ? ldg2(other + (size_t)(i0 - 1) * W + k0) : zero;
+        double2 mid = act ? ldg2(other + (size_t)i0 * W + k0) : zero;
+        for (int i = i0; i <= i1; ++i) {
+            const size_t row = (size_t)i * W;
+            const double2 dn = act ? ldg2(other + row + W + k0) : zero;
+            const double2 f2 = act ? ldg2(hf + row + k0) : zero;
+            const double2 me = act ? ldg2(self + row + k0) : zero;
+            const int p = (i + COLOUR) & 1;
+            double w0, e0, w1, e1;
+            if (p == 0) {
+                double prev = __shfl_up_sync(0xffffffffu, mid.y, 1);
+                if (lane == 0) prev = (act && k0 > 0) ? __ldg(other + row + k0 - 1) : 0.0;
+                w0 = prev; e0 = mid.x; w1 = mid.x; e1 = mid.y;
+            } else {
+                double next = __shfl_down_sync(0xffffffffu, mid.x, 1);
+                if (lane == 31) next = (k0 + 2 < kact) ? __ldg(other + row + k0 + 2) : 0.0;
+                w0 = mid.x; e0 = mid.y; w1 = mid.y; e1 = next;
+            }
+            const int j0 = 2 * k0 + p;
+            if (act && j0 >= 1 && j0 <= n) {
+                double s = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(f2.x, up.x), dn.x), w0), e0);
+                double r = __dadd_rn(s, -__dmul_rn(4.0, me.x));
+                acc = __fma_rn(r, r, acc);
+            }
+            if (act && j0 + 2 <= n) {
+                double s = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(f2.y, up.y), dn.y), w1), e1);
+                double r = __dadd_rn(s, -__dmul_rn(4.0, me.y));
+                acc = __fma_rn(r, r, acc);
+            }
+            up = mid;
+            mid = dn;
+        }
+    }
+    const double t = block_sum<kSweepThreads>(acc, red_smem);
+    if (threadIdx.x == 0)
+        partials[(size_t)COLOUR * gridDim.x * gridDim.y + (size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// Sum of `count` partials in a fixed order -> *out.
+__global__ void __launch_bounds__(kFinalThreads)
+final_sum_kernel(const double *__restrict__ partials, int count, double *__restrict__ out) {
+    __shared__ double smem[kFinalThreads / 32];
+    double v = 0.0;
+    for (int q = threadIdx.x; q < count; q += kFinalThreads) v = __dadd_rn(v, partials[q]);
+    const double t = block_sum<kFinalThreads>(v, smem);
+    if (threadIdx.x == 0) *out = t;
+}
+
+__device__ __forceinline__ double at(const double *const *u, int W, int i, int j) {
+    return u[(i + j) & 1][(size_t)i * W + (j >> 1)];
+}
+
+struct ColourPtrs { const double *p[2]; };
+
+// Partial sums of (h^2 b)^2: h2f plus, in N, S, W, E order, the neighbours on the ring.
+__global__ void __launch_bounds__(256)
+rhs_norm_kernel(ColourPtrs u, ColourPtrs hf, int n, int W, double *__restrict__ partials) {
+    __shared__ double smem[256 / 32];
+    double acc = 0.0;
+    const size_t total = (size_t)n * n;
+    for (size_t q = (size_t)blockIdx.x * 256 + threadIdx.x; q < total; q += (size_t)gridDim.x * 256) {
+        const int i = 1 + (int)(q / n), j = 1 + (int)(q % n);
+        double b = at(hf.p, W, i, j);
+        if (i == 1) b = __dadd_rn(b, at(u.p, W, 0, j));
+        if (i == n) b = __dadd_rn(b, at(u.p, W, n + 1, j));
+        if (j == 1) b = __dadd_rn(b, at(u.p, W, i, 0));
+        if (j == n) b = __dadd_rn(b, at(u.p, W, i, n + 1));
+        acc = __fma_rn(b, b, acc);
+    }
+    const double t = block_sum<256>(acc, smem);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+int residual_rows(int n, int kact) {
+    // enough blocks to fill the GPU, at most kMaxPartials / 2 per colour
+    const int bx = (kact + 2 * kSweepThreads - 1) / (2 * kSweepThreads);
+    int rows = 16;
+    while ((size_t)bx * ((n + rows - 1) / rows) > (size_t)kMaxPartials / 2) rows *= 2;
+    return rows;
+}
+
+}  // namespace
+
+rbgs_status launch_residual_sum(const rbgs_ctx *c, cudaStream_t s) {
+    const Geometry &g = c->g;
+    const int kact = active_width(g.n);
+    const int rows = residual_rows(g.n, kact);
+    dim3 grid((kact + 2 * kSweepThreads - 1) / (2 * kSweepThreads), (g.n + rows - 1) / rows);
+    residual_colour_kernel<0><<<grid, kSweepThreads, 0, s>>>(c->u[0], c->u[1], c->hf[0], g.n, g.W,
+                                                             kact, rows, c->partials);
+    RBGS_LAUNCH_CHECK();
+    residual_colour_kernel<1><<<grid, kSweepThreads, 0, s>>>(c->u[1], c->u[0], c->hf[1], g.n, g.W,
+                                                             kact, rows, c->partials);
+    RBGS_LAUNCH_CHECK();
+    final_sum_kernel<<<1, kFinalThreads, 0, s>>>(c->partials, 2 * (int)(grid.x * grid.y), c->dsum);
+    RBGS_LAUNCH_CHECK();
+    return RBGS_OK;
+}
+
+rbgs_status launch_rhs_norm(const rbgs_ctx *c, cudaStream_t s) {
+    const Geometry &g = c->g;
+    ColourPtrs u{{c->u[0], c->u[1]}}, hf{{c->hf[0], c->hf[1]}};
+    size_t total = (size_t)g.n * g.n;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    rhs_norm_kernel<<<blocks, 256, 0, s>>>(u, hf, g.n, g.W, c->partials);
+    RBGS_LAUNCH_CHECK();
+    final_sum_kernel<<<1, kFinalThreads, 0, s>>>(c->partials, blocks, c->dsum + 1);
+    RBGS_LAUNCH_CHECK();
+    return RBGS_OK;
+}
+
+}  // namespace rbgs

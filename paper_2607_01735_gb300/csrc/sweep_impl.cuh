@@ -1,0 +1,57 @@
+// Device helpers shared by the sweep and residual kernels.
+#pragma once
+
+#include "common.cuh"
+#include "fp64.cuh"
+
+namespace rbgs {
+
+constexpr int kSweepThreads = 128;
+
+// Number of colour values per row that can hold a grid point: ceil((n+2)/2), rounded up
+// to even so that threads always own whole 16-byte pairs.  Always <= W.
+__host__ __device__ inline int active_width(int n) { return (((n + 3) / 2) + 1) & ~1; }
+
+__device__ __forceinline__ double2 ldg2(const double *p) {
+    return __ldg(reinterpret_cast<const double2 *>(p));
+}
+
+__device__ __forceinline__ void stg2(double *p, double2 v) {
+    *reinterpret_cast<double2 *>(p) = v;
+}
+
+// (((hf + vn) + vs) + vw) + ve, times 0.25.  Bit q of M routes add q to the integer pipe.
+template <int M, bool PLAIN>
+__device__ __forceinline__ double update_f64(double hf, double vn, double vs, double vw, double ve) {
+    if (PLAIN) {
+        double s = __dadd_rn(hf, vn);
+        s = __dadd_rn(s, vs);
+        s = __dadd_rn(s, vw);
+        s = __dadd_rn(s, ve);
+        return __dmul_rn(s, 0.25);
+    }
+    double s = (M & 1) ? add_int(hf, vn) : add_fma(hf, vn);
+    s = (M & 2) ? add_int(s, vs) : add_fma(s, vs);
+    s = (M & 4) ? add_int(s, vw) : add_fma(s, vw);
+    s = (M & 8) ? add_int(s, ve) : add_fma(s, ve);
+    return quarter(s);
+}
+
+// Block-wide sum of one double per thread, fixed reduction tree (deterministic).
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double *smem) {
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = (lane < THREADS / 32) ? smem[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t = __dadd_rn(t, __shfl_down_sync(0xffffffffu, t, o));
+    }
+    return t;  // valid in thread 0
+}
+
+bool emulation_split_supported(int m);
+
+}  // namespace rbgs

@@ -1,0 +1,82 @@
+"""The C-ABI library loads and exports every entry point include/rbgs.h declares, and its
+argument checking works without a GPU (host logic only: no CUDA work is issued)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2607_01735_gb300 as rb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rbgs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2607_01735_gb300 import build
+    build.build_library()
+    return rb.load_library()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rbgs_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_names():
+    assert set(_declared()) == set(rb.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    # and the shared object really exports them (dynamic symbol table)
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", rb.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (rbgs_\w+)", out))
+    assert set(_declared()) <= exported
+
+
+def test_default_opts(lib):
+    o = rb.default_opts()
+    assert (o.precision, o.kernel, o.check_every, o.fp64_emulate) == (rb.RBGS_FP64, rb.RBGS_KERNEL_AUTO, 100, -1)
+    assert o.max_sweeps == 1000000000
+
+
+def test_struct_layouts_match_header(lib):
+    # rbgs_opts: 3 ints, a long, 4 ints -> 40 bytes on LP64; problem/result as declared
+    assert ctypes.sizeof(rb.Opts) == 40
+    assert ctypes.sizeof(rb.Problem) == 32
+    assert ctypes.sizeof(rb.Result) == 32
+
+
+def test_argument_errors_without_gpu(lib):
+    f = np.zeros((4, 4))
+    u = np.zeros((6, 6))
+    h = ctypes.c_void_p()
+    assert lib.rbgs_create(0, 0.04, f.ctypes.data, u.ctypes.data, None, None, ctypes.byref(h)) == rb.RBGS_EINVAL
+    assert "n = 0" in rb.rbgs_last_error()
+    assert lib.rbgs_create(4, -1.0, f.ctypes.data, u.ctypes.data, None, None, ctypes.byref(h)) == rb.RBGS_EINVAL
+    assert lib.rbgs_create(4, 0.04, None, u.ctypes.data, None, None, ctypes.byref(h)) == rb.RBGS_EINVAL
+    assert lib.rbgs_create(4, 0.04, f.ctypes.data, u.ctypes.data, None, None, None) == rb.RBGS_EINVAL
+    bad = rb.default_opts(precision=7)
+    assert lib.rbgs_create(4, 0.04, f.ctypes.data, u.ctypes.data, ctypes.byref(bad), None,
+                           ctypes.byref(h)) == rb.RBGS_EINVAL
+    bad = rb.default_opts(fp64_emulate=0x33)
+    assert lib.rbgs_create(4, 0.04, f.ctypes.data, u.ctypes.data, ctypes.byref(bad), None,
+                           ctypes.byref(h)) == rb.RBGS_EINVAL
+    assert lib.rbgs_sweep(None, 1) == rb.RBGS_EINVAL
+    assert lib.rbgs_residual(None, None) == rb.RBGS_EINVAL
+    assert lib.rbgs_solve(None, 1e-8, None, None) == rb.RBGS_EINVAL
+    assert lib.rbgs_get_solution(None, None) == rb.RBGS_EINVAL
+    lib.rbgs_destroy(None)  # ignored
+
+
+def test_binding_rejects_wrong_dtypes(lib):
+    with pytest.raises(TypeError):
+        rb._ptr(np.zeros(4, dtype=np.float32))
+    with pytest.raises(TypeError):
+        rb._ptr(np.zeros((4, 4))[:, ::2])
