@@ -178,6 +178,7 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     c->kernel = o.kernel == RBGS_KERNEL_AUTO ? RBGS_KERNEL_COLOUR : o.kernel;
     c->emulate = o.fp64_emulate == -1 ? 0x00 : o.fp64_emulate;
     c->tile_rows = o.tile_rows ? o.tile_rows : 32;
+    if (c->tile_rows < (n + 65534) / 65535) c->tile_rows = (n + 65534) / 65535;  // grid.y limit
     c->tblock_k = o.tblock_k;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();

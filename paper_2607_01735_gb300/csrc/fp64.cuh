@@ -14,8 +14,8 @@
 //    normal operands whose sum is normal; any other case (a zero or subnormal operand,
 //    Inf/NaN, an exactly cancelling or subnormal sum, overflow past the largest
 //    exponent before rounding) falls back to the hardware add.
-//  * add_fma(a, b): a + b computed as fma(a, 1, b): one rounding of the exact sum, the
-//    same value as the add instruction.
+//  * add_fma(a, b, one): a + b computed as fma(a, one, b) with one == 1.0: one rounding
+//    of the exact sum, the same value as the add instruction.
 //
 // The functions are __host__ __device__ so that the host test harness can check them
 // against the CPU's own IEEE addition.
@@ -40,14 +40,18 @@ inline double hw_add(double a, double b) { volatile double s = a + b; return s; 
 inline double hw_mul(double a, double b) { volatile double p = a * b; return p; }
 #endif
 
-// s * 0.25, exactly as the multiply would round it.
+// s * 0.25, exactly as the multiply would round it.  The multiply on the rare path is
+// an opaque instruction so that the compiler cannot evaluate it speculatively on the
+// common path (that would put it back on the FP64 pipe for every update).
 __host__ __device__ __forceinline__ double quarter(double s) {
 #if defined(__CUDA_ARCH__)
     int hi = __double2hiint(s);
     int lo = __double2loint(s);
     unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
     if (e - 3u <= 2043u) return __hiloint2double(hi - (2 << 20), lo);
-    return __dmul_rn(s, 0.25);
+    double r;
+    asm volatile("mul.rn.f64 %0, %1, 0d3FD0000000000000;" : "=d"(r) : "d"(s));
+    return r;
 #else
     uint64_t u = dbits(s);
     unsigned e = (unsigned)(u >> 52) & 0x7FFu;
@@ -56,11 +60,15 @@ __host__ __device__ __forceinline__ double quarter(double s) {
 #endif
 }
 
-// a + b via a fused multiply-add with unit multiplier (identical result to the add).
-__host__ __device__ __forceinline__ double add_fma(double a, double b) {
+// a + b computed as fma(a, one, b) with one == 1.0: one rounding of the exact sum, the
+// same value as the add instruction.  `one` must come from run-time data (a kernel
+// argument) so that the compiler keeps the fused multiply-add, which GB300 issues at a
+// higher rate than the add.
+__host__ __device__ __forceinline__ double add_fma(double a, double b, double one) {
 #if defined(__CUDA_ARCH__)
-    return __fma_rn(a, 1.0, b);
+    return __fma_rn(a, one, b);
 #else
+    (void)one;
     return hw_add(a, b);
 #endif
 }

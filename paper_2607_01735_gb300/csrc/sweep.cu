@@ -12,7 +12,7 @@
 //
 // Arithmetic.  Each update is (((h2f + N) + S) + W) + E, times 0.25, every step
 // correctly rounded (see fp64.cuh).  Template parameter M picks, per add, the FP64 pipe
-// (fma(a, 1, b)) or the exact integer-pipe add; bits 0-3 are the four adds of the
+// (fma(a, one, b), one = 1.0 passed at run time) or the exact integer-pipe add; bits 0-3 are the four adds of the
 // thread's first point, bits 4-7 of its second.  PLAIN selects the textbook add and
 // multiply instructions.  Every choice yields the same bits.
 #include "common.cuh"
@@ -25,7 +25,8 @@ namespace {
 template <int COLOUR, int M, bool PLAIN>
 __global__ void __launch_bounds__(kSweepThreads)
 half_sweep_f64(double *__restrict__ self, const double *__restrict__ other,
-               const double *__restrict__ hf, int n, int W, int kact, int rows_per_block) {
+               const double *__restrict__ hf, int n, int W, int kact, int rows_per_block,
+               double one) {
     const int lane = threadIdx.x & 31;
     const int k0 = 2 * (blockIdx.x * kSweepThreads + threadIdx.x);
     const bool act = k0 < kact;
@@ -50,8 +51,8 @@ half_sweep_f64(double *__restrict__ self, const double *__restrict__ other,
             if (lane == 31) next = (k0 + 2 < kact) ? __ldg(other + row + k0 + 2) : 0.0;
             w0 = mid.x; e0 = mid.y; w1 = mid.y; e1 = next;
         }
-        const double r0 = update_f64<(M & 15), PLAIN>(f2.x, up.x, dn.x, w0, e0);
-        const double r1 = update_f64<(M >> 4), PLAIN>(f2.y, up.y, dn.y, w1, e1);
+        const double r0 = update_f64<(M & 15), PLAIN>(f2.x, up.x, dn.x, w0, e0, one);
+        const double r1 = update_f64<(M >> 4), PLAIN>(f2.y, up.y, dn.y, w1, e1, one);
         const int j0 = 2 * k0 + p;  // natural column of the first value; second is j0 + 2
         const bool in0 = act && j0 >= 1 && j0 <= n;
         const bool in1 = act && j0 + 2 <= n;
@@ -75,10 +76,10 @@ rbgs_status launch_colour(const rbgs_ctx *c, int colour, cudaStream_t s) {
     dim3 grid((kact + 2 * kSweepThreads - 1) / (2 * kSweepThreads), (g.n + rows - 1) / rows);
     if (colour == 0)
         half_sweep_f64<0, M, PLAIN><<<grid, kSweepThreads, 0, s>>>(c->u[0], c->u[1], c->hf[0],
-                                                                    g.n, g.W, kact, rows);
+                                                                    g.n, g.W, kact, rows, 1.0);
     else
         half_sweep_f64<1, M, PLAIN><<<grid, kSweepThreads, 0, s>>>(c->u[1], c->u[0], c->hf[1],
-                                                                    g.n, g.W, kact, rows);
+                                                                    g.n, g.W, kact, rows, 1.0);
     RBGS_LAUNCH_CHECK();
     return RBGS_OK;
 }

@@ -22,7 +22,8 @@ __device__ __forceinline__ void stg2(double *p, double2 v) {
 
 // (((hf + vn) + vs) + vw) + ve, times 0.25.  Bit q of M routes add q to the integer pipe.
 template <int M, bool PLAIN>
-__device__ __forceinline__ double update_f64(double hf, double vn, double vs, double vw, double ve) {
+__device__ __forceinline__ double update_f64(double hf, double vn, double vs, double vw, double ve,
+                                             double one) {
     if (PLAIN) {
         double s = __dadd_rn(hf, vn);
         s = __dadd_rn(s, vs);
@@ -30,10 +31,10 @@ __device__ __forceinline__ double update_f64(double hf, double vn, double vs, do
         s = __dadd_rn(s, ve);
         return __dmul_rn(s, 0.25);
     }
-    double s = (M & 1) ? add_int(hf, vn) : add_fma(hf, vn);
-    s = (M & 2) ? add_int(s, vs) : add_fma(s, vs);
-    s = (M & 4) ? add_int(s, vw) : add_fma(s, vw);
-    s = (M & 8) ? add_int(s, ve) : add_fma(s, ve);
+    double s = (M & 1) ? add_int(hf, vn) : add_fma(hf, vn, one);
+    s = (M & 2) ? add_int(s, vs) : add_fma(s, vs, one);
+    s = (M & 4) ? add_int(s, vw) : add_fma(s, vw, one);
+    s = (M & 8) ? add_int(s, ve) : add_fma(s, ve, one);
     return quarter(s);
 }
 
