@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--sweeps", type=int, default=200)
     p.add_argument("--emulate", type=int, default=-1, help="FP64 add split (-1: library default)")
     p.add_argument("--tile-rows", type=int, default=0)
+    p.add_argument("--values", type=int, default=0, help="values per thread in a half-sweep (0 auto, 2, 4)")
     p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one launch per colour, 2 temporal")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -243,7 +244,8 @@ def main():
     f = synth.uniform_pm1_grid(n, 1, device=dev)
     u0 = torch.zeros(n + 2, n + 2, dtype=torch.float64, device=dev)
     out = torch.empty_like(u0)
-    opts = rb.default_opts(fp64_emulate=args.emulate, tile_rows=args.tile_rows, kernel=args.kernel)
+    opts = rb.default_opts(fp64_emulate=args.emulate, tile_rows=args.tile_rows, kernel=args.kernel,
+                           sweep_values=args.values)
     lib = rb.load_library()
     stream = torch.cuda.current_stream(dev)
 
@@ -335,6 +337,7 @@ def main():
             "config": {"workload": workload(n, sweeps), "n": n, "sweeps": sweeps,
                        "kernel": "one launch per colour" if args.kernel in (0, 1) else "temporal",
                        "fp64_emulate": emulate_used, "tile_rows": args.tile_rows or "auto",
+                       "sweep_values": args.values or "auto",
                        "l2": "inputs larger than L2 (4 colour arrays of 1.08 GB each)",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs_algorithmic": BYTES_PER_LUP * lups / elapsed / 1e9,

@@ -68,6 +68,7 @@ typedef struct {
     int tile_rows;     /* rows per thread block (0: automatic)                             */
     int fp64_emulate;  /* FP64 adds issued on the integer pipe per 8 (-1: automatic)       */
     int inner_sweeps;  /* FP32 sweeps per defect correction for RBGS_FP32_REFINE (0: auto) */
+    int sweep_values;  /* values each thread updates per row in a half-sweep: 2 or 4 (0: auto) */
 } rbgs_opts;
 
 /* Fills *opts with the defaults (all automatic). */

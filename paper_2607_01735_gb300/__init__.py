@@ -45,7 +45,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("max_sweeps", ctypes.c_long),
                 ("tblock_k", ctypes.c_int), ("tile_rows", ctypes.c_int),
-                ("fp64_emulate", ctypes.c_int), ("inner_sweeps", ctypes.c_int)]
+                ("fp64_emulate", ctypes.c_int), ("inner_sweeps", ctypes.c_int),
+                ("sweep_values", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):

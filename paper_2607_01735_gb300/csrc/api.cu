@@ -165,6 +165,9 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     if (o.fp64_emulate != -1 && !emulation_split_supported(o.fp64_emulate)) {
         set_error("unsupported fp64_emulate %d", o.fp64_emulate); return RBGS_EINVAL;
     }
+    if (o.sweep_values != 0 && o.sweep_values != 2 && o.sweep_values != 4) {
+        set_error("sweep_values must be 0, 2 or 4"); return RBGS_EINVAL;
+    }
     if (o.tile_rows < 0 || o.tblock_k < 0 || o.inner_sweeps < 0) {
         set_error("negative tile_rows / tblock_k / inner_sweeps"); return RBGS_EINVAL;
     }
@@ -180,6 +183,7 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     c->tile_rows = o.tile_rows ? o.tile_rows : 32;
     if (c->tile_rows < (n + 65534) / 65535) c->tile_rows = (n + 65534) / 65535;  // grid.y limit
     c->tblock_k = o.tblock_k;
+    c->pts = o.sweep_values ? o.sweep_values : 2;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
         delete c;

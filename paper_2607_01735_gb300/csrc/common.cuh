@@ -94,6 +94,7 @@ struct rbgs_ctx {
     int kernel;                 // resolved rbgs_kernel
     int emulate;                // resolved FP64 emulation split
     int tile_rows;              // resolved rows per block
+    int pts;                    // values per thread in the half-sweep (2 or 4)
     int tblock_k;               // resolved temporal depth
 };
 

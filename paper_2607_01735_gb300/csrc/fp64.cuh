@@ -40,17 +40,21 @@ inline double hw_add(double a, double b) { volatile double s = a + b; return s; 
 inline double hw_mul(double a, double b) { volatile double p = a * b; return p; }
 #endif
 
-// s * 0.25, exactly as the multiply would round it.  The multiply on the rare path is
-// an opaque instruction so that the compiler cannot evaluate it speculatively on the
-// common path (that would put it back on the FP64 pipe for every update).
+// s * 0.25, exactly as the multiply would round it.  On the device the multiply of the
+// rare path sits behind a warp vote and an opaque instruction, so that the compiler can
+// neither evaluate it speculatively nor predicate it into the common path (either would
+// put an FP64 instruction back on the pipe for every update).  All 32 lanes of the warp
+// must call it together.
 __host__ __device__ __forceinline__ double quarter(double s) {
 #if defined(__CUDA_ARCH__)
-    int hi = __double2hiint(s);
-    int lo = __double2loint(s);
-    unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
-    if (e - 3u <= 2043u) return __hiloint2double(hi - (2 << 20), lo);
-    double r;
-    asm volatile("mul.rn.f64 %0, %1, 0d3FD0000000000000;" : "=d"(r) : "d"(s));
+    const int hi = __double2hiint(s);
+    const int lo = __double2loint(s);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
+    const bool fast = e - 3u <= 2043u;
+    double r = __hiloint2double(hi - (2 << 20), lo);
+    if (__any_sync(0xffffffffu, !fast)) {
+        if (!fast) asm volatile("mul.rn.f64 %0, %1, 0d3FD0000000000000;" : "=d"(r) : "d"(s));
+    }
     return r;
 #else
     uint64_t u = dbits(s);
@@ -113,11 +117,20 @@ __host__ __device__ __forceinline__ double add_int_core(double a, double b, bool
     return bitsd(res);
 }
 
-// a + b, exactly rounded: the integer-pipe add where it applies, else the hardware add.
+// a + b, exactly rounded: the integer-pipe add where it applies, else the hardware add
+// (behind a warp vote and an opaque instruction on the device, as in quarter(); all 32
+// lanes must call it together).
 __host__ __device__ __forceinline__ double add_int(double a, double b) {
     bool ok;
-    const double r = add_int_core(a, b, ok);
+    double r = add_int_core(a, b, ok);
+#if defined(__CUDA_ARCH__)
+    if (__any_sync(0xffffffffu, !ok)) {
+        if (!ok) asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+    }
+    return r;
+#else
     return ok ? r : hw_add(a, b);
+#endif
 }
 
 }  // namespace rbgs

@@ -1,8 +1,8 @@
 // Half-sweep kernels: one launch updates every point of one colour (Section 2, Eq. (1);
 // the red-then-black phases of Algorithm 1), reading only the other colour.
 //
-// Work decomposition.  A thread owns two neighbouring values (k0, k0+1) of its colour
-// in a row, loaded and stored as one 16-byte vector, and walks down `rows` consecutive
+// Work decomposition.  A thread owns PTS (2 or 4) neighbouring values k0.. of its colour
+// in a row, loaded and stored as 16-byte vectors, and walks down `rows` consecutive
 // rows of a strip.  The other colour's rows i-1, i, i+1 live in registers as the strip
 // advances, so every value of the other colour is loaded from memory once per strip
 // (plus the two rows shared with neighbouring strips), h2*f once, and the own colour is
@@ -12,9 +12,9 @@
 //
 // Arithmetic.  Each update is (((h2f + N) + S) + W) + E, times 0.25, every step
 // correctly rounded (see fp64.cuh).  Template parameter M picks, per add, the FP64 pipe
-// (fma(a, one, b), one = 1.0 passed at run time) or the exact integer-pipe add; bits 0-3 are the four adds of the
-// thread's first point, bits 4-7 of its second.  PLAIN selects the textbook add and
-// multiply instructions.  Every choice yields the same bits.
+// (fma(a, one, b), one = 1.0 passed at run time) or the exact integer-pipe add; bits 0-3
+// are the four adds of the thread's even values, bits 4-7 of its odd values.  PLAIN
+// selects the textbook add and multiply instructions.  Every choice yields the same bits.
 #include "common.cuh"
 #include "fp64.cuh"
 #include "sweep_impl.cuh"
@@ -22,87 +22,101 @@
 namespace rbgs {
 namespace {
 
-template <int COLOUR, int M, bool PLAIN>
+// PTS values per thread (2 or 4): more values give the FP64 pipe more independent
+// update chains per thread.
+template <int COLOUR, int M, bool PLAIN, int PTS>
 __global__ void __launch_bounds__(kSweepThreads)
 half_sweep_f64(double *__restrict__ self, const double *__restrict__ other,
                const double *__restrict__ hf, int n, int W, int kact, int rows_per_block,
                double one) {
+    static_assert(PTS == 2 || PTS == 4, "2 or 4 values per thread");
     const int lane = threadIdx.x & 31;
-    const int k0 = 2 * (blockIdx.x * kSweepThreads + threadIdx.x);
-    const bool act = k0 < kact;
+    const int k0 = PTS * (blockIdx.x * kSweepThreads + threadIdx.x);
+    const bool act = k0 < kact;  // k0 + PTS - 1 < W as W is a multiple of 32
     const int i0 = 1 + blockIdx.y * rows_per_block;
     if (i0 > n) return;  // uniform over the block
     const int i1 = min(n, i0 + rows_per_block - 1);
-    const double2 zero = make_double2(0.0, 0.0);
-    double2 up = act ? ldg2(other + (size_t)(i0 - 1) * W + k0) : zero;
-    double2 mid = act ? ldg2(other + (size_t)i0 * W + k0) : zero;
+    double up[PTS], mid[PTS], dn[PTS], f[PTS], r[PTS];
+    load_row<PTS>(up, other + (size_t)(i0 - 1) * W + k0, act);
+    load_row<PTS>(mid, other + (size_t)i0 * W + k0, act);
     for (int i = i0; i <= i1; ++i) {
         const size_t row = (size_t)i * W;
-        const double2 dn = act ? ldg2(other + row + W + k0) : zero;
-        const double2 f2 = act ? ldg2(hf + row + k0) : zero;
+        load_row<PTS>(dn, other + row + W + k0, act);
+        load_row<PTS>(f, hf + row + k0, act);
         const int p = (i + COLOUR) & 1;  // column offset of this colour in row i
-        double w0, e0, w1, e1;
         if (p == 0) {
-            double prev = __shfl_up_sync(0xffffffffu, mid.y, 1);
+            // value q sits at natural column 2(k0+q): west = other[k0+q-1], east = other[k0+q]
+            double prev = __shfl_up_sync(0xffffffffu, mid[PTS - 1], 1);
             if (lane == 0) prev = (act && k0 > 0) ? __ldg(other + row + k0 - 1) : 0.0;
-            w0 = prev; e0 = mid.x; w1 = mid.x; e1 = mid.y;
+#pragma unroll
+            for (int q = 0; q < PTS; ++q)
+                r[q] = update_f64<PLAIN>((M >> (4 * (q & 1))) & 15, f[q], up[q], dn[q],
+                                         q ? mid[q - 1] : prev, mid[q], one);
         } else {
-            double next = __shfl_down_sync(0xffffffffu, mid.x, 1);
-            if (lane == 31) next = (k0 + 2 < kact) ? __ldg(other + row + k0 + 2) : 0.0;
-            w0 = mid.x; e0 = mid.y; w1 = mid.y; e1 = next;
+            // value q sits at 2(k0+q)+1: west = other[k0+q], east = other[k0+q+1]
+            double next = __shfl_down_sync(0xffffffffu, mid[0], 1);
+            if (lane == 31) next = (k0 + PTS < kact) ? __ldg(other + row + k0 + PTS) : 0.0;
+#pragma unroll
+            for (int q = 0; q < PTS; ++q)
+                r[q] = update_f64<PLAIN>((M >> (4 * (q & 1))) & 15, f[q], up[q], dn[q], mid[q],
+                                         q + 1 < PTS ? mid[q + 1] : next, one);
         }
-        const double r0 = update_f64<(M & 15), PLAIN>(f2.x, up.x, dn.x, w0, e0, one);
-        const double r1 = update_f64<(M >> 4), PLAIN>(f2.y, up.y, dn.y, w1, e1, one);
-        const int j0 = 2 * k0 + p;  // natural column of the first value; second is j0 + 2
-        const bool in0 = act && j0 >= 1 && j0 <= n;
-        const bool in1 = act && j0 + 2 <= n;
+        const int j0 = 2 * k0 + p;  // natural column of value 0; value q is at j0 + 2q
         double *sp = self + row + k0;
-        if (in0 && in1) {
-            stg2(sp, make_double2(r0, r1));
-        } else {
-            if (in0) sp[0] = r0;
-            if (in1) sp[1] = r1;
+        if (act && j0 >= 1 && j0 + 2 * (PTS - 1) <= n) {
+            store_row<PTS>(sp, r);
+        } else if (act) {
+#pragma unroll
+            for (int q = 0; q < PTS; ++q)
+                if (j0 + 2 * q >= 1 && j0 + 2 * q <= n) sp[q] = r[q];
         }
-        up = mid;
-        mid = dn;
+#pragma unroll
+        for (int q = 0; q < PTS; ++q) {
+            up[q] = mid[q];
+            mid[q] = dn[q];
+        }
     }
 }
 
-template <int M, bool PLAIN>
+template <int M, bool PLAIN, int PTS>
 rbgs_status launch_colour(const rbgs_ctx *c, int colour, cudaStream_t s) {
     const Geometry &g = c->g;
     const int kact = active_width(g.n);
     const int rows = c->tile_rows;
-    dim3 grid((kact + 2 * kSweepThreads - 1) / (2 * kSweepThreads), (g.n + rows - 1) / rows);
+    const int per_block = PTS * kSweepThreads;
+    dim3 grid((kact + per_block - 1) / per_block, (g.n + rows - 1) / rows);
     if (colour == 0)
-        half_sweep_f64<0, M, PLAIN><<<grid, kSweepThreads, 0, s>>>(c->u[0], c->u[1], c->hf[0],
-                                                                    g.n, g.W, kact, rows, 1.0);
+        half_sweep_f64<0, M, PLAIN, PTS><<<grid, kSweepThreads, 0, s>>>(c->u[0], c->u[1], c->hf[0],
+                                                                         g.n, g.W, kact, rows, 1.0);
     else
-        half_sweep_f64<1, M, PLAIN><<<grid, kSweepThreads, 0, s>>>(c->u[1], c->u[0], c->hf[1],
-                                                                    g.n, g.W, kact, rows, 1.0);
+        half_sweep_f64<1, M, PLAIN, PTS><<<grid, kSweepThreads, 0, s>>>(c->u[1], c->u[0], c->hf[1],
+                                                                         g.n, g.W, kact, rows, 1.0);
     RBGS_LAUNCH_CHECK();
     return RBGS_OK;
+}
+
+template <int PTS>
+rbgs_status launch_pts(const rbgs_ctx *c, int colour, cudaStream_t s) {
+    switch (c->emulate) {
+    case -2: return launch_colour<0x00, true, PTS>(c, colour, s);
+    case 0x00: return launch_colour<0x00, false, PTS>(c, colour, s);
+    case 0x08: return launch_colour<0x08, false, PTS>(c, colour, s);
+    case 0x88: return launch_colour<0x88, false, PTS>(c, colour, s);
+    case 0x8C: return launch_colour<0x8C, false, PTS>(c, colour, s);
+    case 0xCC: return launch_colour<0xCC, false, PTS>(c, colour, s);
+    case 0xFF: return launch_colour<0xFF, false, PTS>(c, colour, s);
+    default:
+        set_error("unsupported FP64 emulation split 0x%x", c->emulate);
+        return RBGS_EINVAL;
+    }
 }
 
 }  // namespace
 
 // emulate: -2 = textbook add/multiply instructions; otherwise the mask of integer-pipe
-// adds (a few tuned splits are instantiated; others round to the nearest below).
+// adds (bits 0-3: the four adds of even values, bits 4-7: of odd values).
 rbgs_status launch_half_sweep(const rbgs_ctx *c, int colour, cudaStream_t s) {
-    switch (c->emulate) {
-    case -2: return launch_colour<0x00, true>(c, colour, s);
-    case 0x00: return launch_colour<0x00, false>(c, colour, s);
-    case 0x08: return launch_colour<0x08, false>(c, colour, s);
-    case 0x88: return launch_colour<0x88, false>(c, colour, s);
-    case 0x8C: return launch_colour<0x8C, false>(c, colour, s);
-    case 0xCC: return launch_colour<0xCC, false>(c, colour, s);
-    case 0xCE: return launch_colour<0xCE, false>(c, colour, s);
-    case 0xEE: return launch_colour<0xEE, false>(c, colour, s);
-    case 0xFF: return launch_colour<0xFF, false>(c, colour, s);
-    default:
-        set_error("unsupported FP64 emulation split 0x%x", c->emulate);
-        return RBGS_EINVAL;
-    }
+    return c->pts == 4 ? launch_pts<4>(c, colour, s) : launch_pts<2>(c, colour, s);
 }
 
 rbgs_status launch_sweeps_f64(const rbgs_ctx *c, long nsweeps, cudaStream_t s) {
@@ -117,7 +131,7 @@ rbgs_status launch_sweeps_f64(const rbgs_ctx *c, long nsweeps, cudaStream_t s) {
 
 bool emulation_split_supported(int m) {
     switch (m) {
-    case -2: case 0x00: case 0x08: case 0x88: case 0x8C: case 0xCC: case 0xCE: case 0xEE: case 0xFF:
+    case -2: case 0x00: case 0x08: case 0x88: case 0x8C: case 0xCC: case 0xFF:
         return true;
     default:
         return false;

@@ -20,10 +20,27 @@ __device__ __forceinline__ void stg2(double *p, double2 v) {
     *reinterpret_cast<double2 *>(p) = v;
 }
 
-// (((hf + vn) + vs) + vw) + ve, times 0.25.  Bit q of M routes add q to the integer pipe.
-template <int M, bool PLAIN>
-__device__ __forceinline__ double update_f64(double hf, double vn, double vs, double vw, double ve,
-                                             double one) {
+template <int PTS>
+__device__ __forceinline__ void load_row(double *v, const double *p, bool act) {
+#pragma unroll
+    for (int q = 0; q < PTS; q += 2) {
+        const double2 t = act ? ldg2(p + q) : make_double2(0.0, 0.0);
+        v[q] = t.x;
+        v[q + 1] = t.y;
+    }
+}
+
+template <int PTS>
+__device__ __forceinline__ void store_row(double *p, const double *v) {
+#pragma unroll
+    for (int q = 0; q < PTS; q += 2) stg2(p + q, make_double2(v[q], v[q + 1]));
+}
+
+// (((hf + vn) + vs) + vw) + ve, times 0.25.  Bit q of m routes add q to the integer pipe;
+// m is a compile-time constant at every call site (unrolled loops), so the branches fold.
+template <bool PLAIN>
+__device__ __forceinline__ double update_f64(int m, double hf, double vn, double vs, double vw,
+                                             double ve, double one) {
     if (PLAIN) {
         double s = __dadd_rn(hf, vn);
         s = __dadd_rn(s, vs);
@@ -31,10 +48,10 @@ __device__ __forceinline__ double update_f64(double hf, double vn, double vs, do
         s = __dadd_rn(s, ve);
         return __dmul_rn(s, 0.25);
     }
-    double s = (M & 1) ? add_int(hf, vn) : add_fma(hf, vn, one);
-    s = (M & 2) ? add_int(s, vs) : add_fma(s, vs, one);
-    s = (M & 4) ? add_int(s, vw) : add_fma(s, vw, one);
-    s = (M & 8) ? add_int(s, ve) : add_fma(s, ve, one);
+    double s = (m & 1) ? add_int(hf, vn) : add_fma(hf, vn, one);
+    s = (m & 2) ? add_int(s, vs) : add_fma(s, vs, one);
+    s = (m & 4) ? add_int(s, vw) : add_fma(s, vw, one);
+    s = (m & 8) ? add_int(s, ve) : add_fma(s, ve, one);
     return quarter(s);
 }
 

@@ -62,15 +62,16 @@ def _assert_bits(got, ref):
         raise AssertionError(f"{len(bad)} values differ; first at {(i, j)}: {got[i, j]!r} vs {ref[i, j]!r}")
 
 
-SIZES = [1, 2, 3, 4, 5, 6, 7, 8, 9, 16, 31, 32, 33, 63, 64, 127, 255, 256, 257, 300, 509, 1000]
+SIZES = [1, 2, 3, 4, 5, 6, 7, 8, 9, 16, 31, 32, 33, 63, 64, 127, 255, 256, 257, 300, 509, 1000, 1030]
 
 
+@pytest.mark.parametrize("values", [2, 4])
 @pytest.mark.parametrize("n", SIZES)
-def test_bit_exact_against_oracle(n):
+def test_bit_exact_against_oracle(n, values):
     f, u0 = _problem(n, 11 + n)
     h2 = synth.h_squared(n)
     sweeps = 7 if n > 300 else 13
-    got, rho = _run_gpu(n, h2, f, u0, sweeps)
+    got, rho = _run_gpu(n, h2, f, u0, sweeps, sweep_values=values)
     ref = u0.copy()
     oracle.sweeps(ref, f, h2, sweeps)
     _assert_bits(got, ref)
@@ -78,23 +79,25 @@ def test_bit_exact_against_oracle(n):
     assert abs(rho - rho_ref) <= RESID_RTOL * rho_ref
 
 
-@pytest.mark.parametrize("emulate", [-2, 0x00, 0x08, 0x88, 0x8C, 0xCC, 0xCE, 0xEE, 0xFF])
+@pytest.mark.parametrize("values", [2, 4])
+@pytest.mark.parametrize("emulate", [-2, 0x00, 0x08, 0x88, 0x8C, 0xCC, 0xFF])
 @pytest.mark.parametrize("n", [33, 257])
-def test_every_fp64_add_split_is_bit_exact(n, emulate):
+def test_every_fp64_add_split_is_bit_exact(n, emulate, values):
     f, u0 = _problem(n, 100 + n)
     h2 = synth.h_squared(n)
-    got, _ = _run_gpu(n, h2, f, u0, 9, fp64_emulate=emulate)
+    got, _ = _run_gpu(n, h2, f, u0, 9, fp64_emulate=emulate, sweep_values=values)
     ref = u0.copy()
     oracle.sweeps(ref, f, h2, 9)
     _assert_bits(got, ref)
 
 
+@pytest.mark.parametrize("values", [2, 4])
 @pytest.mark.parametrize("rows", [1, 2, 7, 32, 64, 200])
-def test_strip_heights(rows):
+def test_strip_heights(rows, values):
     n = 203
     f, u0 = _problem(n, 300 + rows)
     h2 = synth.h_squared(n)
-    got, _ = _run_gpu(n, h2, f, u0, 5, tile_rows=rows)
+    got, _ = _run_gpu(n, h2, f, u0, 5, tile_rows=rows, sweep_values=values)
     ref = u0.copy()
     oracle.sweeps(ref, f, h2, 5)
     _assert_bits(got, ref)
