@@ -134,6 +134,22 @@ rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, double tol,
                                const rbgs_opts *opts, void *cuda_stream, double **u_out,
                                rbgs_result *res);
 
+/*
+ * Relative residual of a natural-layout iterate without allocating memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate device memory
+ * (a fixed memory budget set at start-up, code running inside an allocator callback, or
+ * code that must avoid the device synchronisation cudaMalloc/cudaFree may imply).
+ * f (N*N), u ((N+2)^2, ring included) and rel_out (one double) must be device memory of
+ * the current device; rho is written to *rel_out asynchronously on the stream, with the
+ * same definition as rbgs_residual.  Its scratch is a fixed array inside the library's
+ * device image (128 KiB, held on every GPU that loads the library until the process
+ * exits), so N <= 32768; larger N returns RBGS_EINVAL.  The first call on each device looks
+ * up that array's device address; make that first call before any stream capture.  Calls
+ * share the array: calls that overlap on the GPU race.  No cudaMalloc/cudaFree is made.
+ */
+rbgs_status rbgs_residual_static(int n, double h2, const double *f, const double *u,
+                                 double *rel_out, void *cuda_stream);
+
 /* Frees the context (NULL is ignored). Synchronises its stream first. */
 void rbgs_destroy(rbgs_t ctx);
 

@@ -30,7 +30,7 @@ RBGS_KERNEL_AUTO, RBGS_KERNEL_COLOUR, RBGS_KERNEL_TEMPORAL = 0, 1, 2
 # Every symbol include/rbgs.h declares.
 EXPORTED = ("rbgs_default_opts", "rbgs_create", "rbgs_sweep", "rbgs_residual", "rbgs_solve",
             "rbgs_get_solution", "rbgs_set_solution", "rbgs_solve_batched", "rbgs_destroy",
-            "rbgs_last_error")
+            "rbgs_last_error", "rbgs_residual_static")
 
 
 class RbgsError(RuntimeError):
@@ -92,6 +92,8 @@ def load_library(path: str | None = None):
     lib.rbgs_solve_batched.restype = c_int
     lib.rbgs_destroy.argtypes = [vp]
     lib.rbgs_destroy.restype = None
+    lib.rbgs_residual_static.argtypes = [c_int, c_double, vp, vp, vp, vp]
+    lib.rbgs_residual_static.restype = c_int
     lib.rbgs_last_error.argtypes = []
     lib.rbgs_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -200,6 +202,13 @@ def rbgs_solve_batched(problems, tol: float, u_out: list, opts: Opts | None = No
         _check(st)
     return [{"status": r.status, "sweeps": r.sweeps, "rel": r.rel, "latency_ms": r.latency_ms}
             for r in res[:k]]
+
+
+def rbgs_residual_static(n: int, h2: float, f, u, rel_out, stream=None) -> None:
+    """rbgs_residual_static: rho of a natural-layout device iterate into rel_out (device,
+    one float64), allocating nothing (for callers that cannot allocate device memory)."""
+    s = _stream_of(f, u, stream=stream)
+    _check(load_library().rbgs_residual_static(int(n), float(h2), _ptr(f), _ptr(u), _ptr(rel_out), s))
 
 
 class Solver:
