@@ -57,6 +57,9 @@ def _load():
         lib.ref_residual_field_f64.restype = None
         lib.ref_solve_f64.argtypes = [c_int, c_int, c_double, dp, dp, c_double, c_int, c_long, dp]
         lib.ref_solve_f64.restype = c_long
+        lib.ref_refine_solve.argtypes = [c_int, c_int, c_double, dp, dp, c_double, c_long, c_long, dp,
+                                         ctypes.POINTER(c_long)]
+        lib.ref_refine_solve.restype = c_long
         _lib = lib
     return _lib
 
@@ -125,6 +128,16 @@ def solve(u, f, h2, tol: float, check_every: int, max_sweeps: int) -> tuple[int,
     done = _load().ref_solve_f64(ni, nj, float(h2), _dptr(f), _dptr(u), float(tol),
                                  int(check_every), int(max_sweeps), ctypes.byref(rho))
     return int(done), rho.value
+
+
+def refine_solve(u, f, h2, tol: float, inner: int, max_sweeps: int) -> tuple[int, float, int]:
+    """Mixed-precision refinement (binary32 sweeps, binary64 defect and correction), in
+    place on u; returns (inner sweeps done, rho, outer steps)."""
+    ni, nj = _check(u, f, np.float64)
+    rho, outer = ctypes.c_double(), ctypes.c_long()
+    done = _load().ref_refine_solve(ni, nj, float(h2), _dptr(f), _dptr(u), float(tol), int(inner),
+                                    int(max_sweeps), ctypes.byref(rho), ctypes.byref(outer))
+    return int(done), rho.value, outer.value
 
 
 def window_value(f_full: np.ndarray, u0_full: np.ndarray, h2: float, nsweeps: int,

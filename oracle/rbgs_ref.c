@@ -168,3 +168,60 @@ long ref_solve_f64(int ni, int nj, double h2, const double *f, double *u, double
     if (rho_out) *rho_out = rho;
     return done;
 }
+
+/*
+ * Mixed-precision iterative refinement (not in the paper: the growth direction in which
+ * the sweeps run in binary32 and only the residual and the correction stay in binary64).
+ * One outer step, in this order:
+ *   1. rt = h^2 (b - A u) pointwise in binary64 (as ref_residual_field_f64), rho, and
+ *      mx = max |rt|;
+ *   2. e with mx = m 2^e, 0.5 <= m < 1 (frexp); r32 = (float)(rt * 2^-e);
+ *   3. d = `inner` binary32 sweeps of the same red-black iteration on
+ *      (4 I - Adj) d = r32, from d = 0 with a zero ring (h^2 f replaced by r32, i.e.
+ *      ref_sweeps_f32 with h2 = 1);
+ *   4. u = u + (double)d * 2^e at interior points.
+ * Stops when rho <= tol (checked before the first step and after each) or after
+ * max_sweeps inner sweeps; the last step is shortened to fit.  Returns the inner sweeps
+ * done; writes rho and the number of outer steps.
+ */
+#include <stdlib.h>
+
+long ref_refine_solve(int ni, int nj, double h2, const double *f, double *u, double tol,
+                      long inner, long max_sweeps, double *rho_out, long *outer_out)
+{
+    size_t m = (size_t)ni * (size_t)nj, g = (size_t)(ni + 2) * (size_t)(nj + 2);
+    double *rt = (double *)malloc(m * sizeof(double));
+    float *r32 = (float *)malloc(m * sizeof(float));
+    float *d = (float *)malloc(g * sizeof(float));
+    long done = 0, outer = 0;
+    double rho = ref_residual_f64(ni, nj, h2, f, u, NULL, NULL);
+    ref_residual_field_f64(ni, nj, h2, f, u, rt);
+    while (!(rho <= tol) && done < max_sweeps && isfinite(rho)) {
+        double mx = 0.0;
+        for (size_t q = 0; q < m; ++q)
+            if (fabs(rt[q]) > mx) mx = fabs(rt[q]);
+        int e = 0;
+        frexp(mx, &e);
+        double down = ldexp(1.0, -e), up = ldexp(1.0, e);
+        for (size_t q = 0; q < m; ++q) r32[q] = (float)(rt[q] * down);
+        for (size_t q = 0; q < g; ++q) d[q] = 0.0f;
+        long k = inner;
+        if (k > max_sweeps - done) k = max_sweeps - done;
+        ref_sweeps_f32(ni, nj, 1.0f, r32, d, k, 0);
+        for (int i = 1; i <= ni; ++i)
+            for (int j = 1; j <= nj; ++j) {
+                size_t q = (size_t)i * (size_t)(nj + 2) + (size_t)j;
+                u[q] = u[q] + (double)d[q] * up;
+            }
+        done += k;
+        outer += 1;
+        rho = ref_residual_f64(ni, nj, h2, f, u, NULL, NULL);
+        ref_residual_field_f64(ni, nj, h2, f, u, rt);
+    }
+    free(rt);
+    free(r32);
+    free(d);
+    if (rho_out) *rho_out = rho;
+    if (outer_out) *outer_out = outer;
+    return done;
+}

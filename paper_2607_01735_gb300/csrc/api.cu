@@ -1,6 +1,7 @@
 // C ABI entry points of librbgs (declared in include/rbgs.h): context life cycle,
-// layout staging, sweep scheduling (direct launches or a cached CUDA graph), residual
-// evaluation and the convergence loop.
+// layout staging, sweep scheduling (direct launches, a cached CUDA graph, or temporally
+// blocked passes), residual evaluation, the convergence loop and the mixed-precision
+// refinement loop.
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -65,10 +66,10 @@ rbgs_status load_problem(rbgs_ctx *c, const double *f, const double *u_init) {
     rbgs_status st;
     if (f) {
         if ((st = stage_in(c, f, (size_t)g.n * g.n, &view)) != RBGS_OK) return st;
-        if ((st = launch_pack_f(g, c->h2, view, c->hf[0], c->hf[1], c->stream)) != RBGS_OK) return st;
+        if ((st = launch_pack_f(g, c->h2, view, c->f64.hf[0], c->f64.hf[1], c->stream)) != RBGS_OK) return st;
     }
     if ((st = stage_in(c, u_init, (size_t)g.rows * g.rows, &view)) != RBGS_OK) return st;
-    if ((st = launch_pack_u(g, view, c->u[0], c->u[1], c->stream)) != RBGS_OK) return st;
+    if ((st = launch_pack_u(g, view, c->f64.u[0], c->f64.u[1], c->stream)) != RBGS_OK) return st;
     // ||h^2 b||^2 depends on f and the ring
     if ((st = launch_rhs_norm(c, c->stream)) != RBGS_OK) return st;
     RBGS_CUDA(cudaMemcpyAsync(c->hsum + 1, c->dsum + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -81,17 +82,73 @@ void free_ctx(rbgs_ctx *c) {
     if (!c) return;
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (int q = 0; q < 2; ++q) {
-        cudaFree(c->u[q]);
-        cudaFree(c->hf[q]);
-        cudaFree(c->d32[q]);
-        cudaFree(c->r32[q]);
+        cudaFree(c->f64.u[q]);
+        cudaFree(c->f64.hf[q]);
+        cudaFree(c->f64.alt[q]);
+        cudaFree(c->f32.u[q]);
+        cudaFree(c->f32.hf[q]);
+        cudaFree(c->f32.alt[q]);
     }
     cudaFree(c->staging);
     cudaFree(c->partials);
     cudaFree(c->dsum);
+    cudaFree(c->dstatus);
     if (c->hsum) cudaFreeHost(c->hsum);
+    if (c->hstatus) cudaFreeHost(c->hstatus);
     if (c->capture) cudaStreamDestroy(c->capture);
     delete c;
+}
+
+// Zero-filled device buffer of `bytes` (stream-ordered fill).
+rbgs_status alloc_zero(void **p, size_t bytes, cudaStream_t s) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error("cudaMalloc of %zu bytes failed", bytes);
+        return RBGS_ENOMEM;
+    }
+    RBGS_CUDA(cudaMemsetAsync(*p, 0, bytes, s));
+    return RBGS_OK;
+}
+
+rbgs_status ensure_f64_alt(rbgs_ctx *c) {
+    if (c->f64.alt[0]) return RBGS_OK;
+    const size_t bytes = c->g.colour_elems() * sizeof(double);
+    for (int q = 0; q < 2; ++q) {
+        rbgs_status st = alloc_zero(reinterpret_cast<void **>(&c->f64.alt[q]), bytes, c->stream);
+        if (st != RBGS_OK) return st;
+    }
+    c->f64.maps_ready = false;
+    return RBGS_OK;
+}
+
+// FP32 correction, scaled defect and (for the temporal inner kernel) the partner buffers.
+rbgs_status ensure_f32(rbgs_ctx *c) {
+    if (c->f32.u[0]) return RBGS_OK;
+    c->f32.n = c->g.n;
+    c->f32.W = colour_width_bytes(c->g.n, 4);
+    const size_t bytes = (size_t)c->g.rows * c->f32.W * sizeof(float);
+    for (int q = 0; q < 2; ++q) {
+        rbgs_status st;
+        if ((st = alloc_zero(reinterpret_cast<void **>(&c->f32.u[q]), bytes, c->stream)) != RBGS_OK) return st;
+        if ((st = alloc_zero(reinterpret_cast<void **>(&c->f32.hf[q]), bytes, c->stream)) != RBGS_OK) return st;
+        if (c->kernel32 == RBGS_KERNEL_TEMPORAL &&
+            (st = alloc_zero(reinterpret_cast<void **>(&c->f32.alt[q]), bytes, c->stream)) != RBGS_OK)
+            return st;
+    }
+    c->f32.maps_ready = false;
+    return RBGS_OK;
+}
+
+// A bounded device-side wait gave up in an earlier launch?  (Reads after a stream sync.)
+rbgs_status check_device_status(rbgs_ctx *c) {
+    RBGS_CUDA(cudaMemcpyAsync(c->hstatus, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    RBGS_CUDA(cudaStreamSynchronize(c->stream));
+    if (*c->hstatus) {
+        set_error("a bounded device-side wait timed out (status %d)", *c->hstatus);
+        return RBGS_ETIMEOUT;
+    }
+    return RBGS_OK;
 }
 
 rbgs_status enqueue_sweeps(rbgs_ctx *c, long nsweeps, cudaStream_t s) {
@@ -122,6 +179,71 @@ rbgs_status ensure_graph(rbgs_ctx *c) {
     }
     c->graph_sweeps = kGraphSweeps;
     return RBGS_OK;
+}
+
+// rho and max |rt| of the current FP64 iterate (synchronises the stream).
+rbgs_status defect_stats(rbgs_ctx *c, double *rho, double *mx) {
+    rbgs_status st = launch_defect(c, false, 1.0, c->stream);
+    if (st != RBGS_OK) return st;
+    RBGS_CUDA(cudaMemcpyAsync(c->hsum, c->dsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((st = check_device_status(c)) != RBGS_OK) return st;
+    const double r2 = c->hsum[0];
+    *mx = c->hsum[2];
+    *rho = c->den2 > 0.0 ? std::sqrt(r2) / std::sqrt(c->den2) : std::sqrt(r2);
+    if (!std::isfinite(*rho)) {
+        set_error("residual is not finite");
+        return RBGS_ENONFINITE;
+    }
+    return RBGS_OK;
+}
+
+rbgs_status inner_sweeps_f32(rbgs_ctx *c, long m) {
+    if (c->kernel32 == RBGS_KERNEL_TEMPORAL) {
+        const int k = c->tblock_k32;
+        const long passes = m / k;
+        for (long q = 0; q < passes; ++q) {
+            rbgs_status st = launch_temporal_pass<float>(c->f32, k, c->dstatus, c->stream);
+            if (st != RBGS_OK) return st;
+        }
+        m -= passes * k;
+    }
+    return launch_sweeps_f32(c->f32, m, c->stream);
+}
+
+// Mixed-precision iterative refinement: FP64 defect and correction, FP32 sweeps.
+rbgs_status refine_solve(rbgs_ctx *c, double tol, long *done_out, double *rho_out) {
+    rbgs_status st = ensure_f32(c);
+    long done = 0;
+    double rho = 0.0, mx = 0.0;
+    if (st == RBGS_OK) st = defect_stats(c, &rho, &mx);
+    while (st == RBGS_OK && !(rho <= tol) && done < c->opts.max_sweeps) {
+        int e = 0;
+        std::frexp(mx, &e);  // mx = m 2^e, m in [0.5, 1)
+        const double down = std::ldexp(1.0, -e), up = std::ldexp(1.0, e);
+        if ((st = launch_defect(c, true, down, c->stream)) != RBGS_OK) break;
+        const size_t bytes = (size_t)c->g.rows * c->f32.W * sizeof(float);
+        for (int q = 0; q < 2; ++q) {
+            if (cudaMemsetAsync(c->f32.u[q], 0, bytes, c->stream) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("cudaMemsetAsync failed");
+                st = RBGS_ECUDA;
+            }
+        }
+        if (st != RBGS_OK) break;
+        long m = c->inner_sweeps;
+        if (m > c->opts.max_sweeps - done) m = c->opts.max_sweeps - done;
+        if ((st = inner_sweeps_f32(c, m)) != RBGS_OK) break;
+        if ((st = launch_correct(c, up, c->stream)) != RBGS_OK) break;
+        done += m;
+        st = defect_stats(c, &rho, &mx);
+    }
+    if (done_out) *done_out = done;
+    if (rho_out) *rho_out = rho;
+    if (st == RBGS_OK && !(rho <= tol)) {
+        set_error("not converged after %ld sweeps (rho = %.3e)", done, rho);
+        st = RBGS_ENOTCONV;
+    }
+    return st;
 }
 
 }  // namespace
@@ -171,6 +293,12 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     if (o.tile_rows < 0 || o.tblock_k < 0 || o.inner_sweeps < 0) {
         set_error("negative tile_rows / tblock_k / inner_sweeps"); return RBGS_EINVAL;
     }
+    if (o.tblock_k && o.precision == RBGS_FP64 && o.tblock_k != 1 && o.tblock_k != 2 && o.tblock_k != 4) {
+        set_error("tblock_k for FP64 sweeps must be 1, 2 or 4"); return RBGS_EINVAL;
+    }
+    if (o.tblock_k && o.precision == RBGS_FP32_REFINE && o.tblock_k != 2 && o.tblock_k != 4 && o.tblock_k != 8) {
+        set_error("tblock_k for FP32 inner sweeps must be 2, 4 or 8"); return RBGS_EINVAL;
+    }
 
     rbgs_ctx *c = new (std::nothrow) rbgs_ctx();
     if (!c) { set_error("out of host memory"); return RBGS_ENOMEM; }
@@ -182,8 +310,15 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     c->emulate = o.fp64_emulate == -1 ? 0x00 : o.fp64_emulate;
     c->tile_rows = o.tile_rows ? o.tile_rows : 32;
     if (c->tile_rows < (n + 65534) / 65535) c->tile_rows = (n + 65534) / 65535;  // grid.y limit
-    c->tblock_k = o.tblock_k;
     c->pts = o.sweep_values ? o.sweep_values : 2;
+    // FP64 sweeps: temporal depth (used when kernel == TEMPORAL)
+    c->tblock_k = (o.precision == RBGS_FP64 && o.tblock_k) ? o.tblock_k : 2;
+    // FP32 inner sweeps of the refinement: temporal tiles for large grids unless told otherwise
+    c->kernel32 = o.kernel == RBGS_KERNEL_AUTO ? (n >= 512 ? RBGS_KERNEL_TEMPORAL : RBGS_KERNEL_COLOUR) : o.kernel;
+    c->tblock_k32 = (o.precision == RBGS_FP32_REFINE && o.tblock_k) ? o.tblock_k : 4;
+    c->inner_sweeps = o.inner_sweeps ? o.inner_sweeps : 100;
+    c->f64.n = n;
+    c->f64.W = c->g.W;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -193,11 +328,14 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     const size_t bytes = c->g.colour_elems() * sizeof(double);
     bool ok = true;
     for (int q = 0; q < 2 && ok; ++q) {
-        ok = cudaMalloc(&c->u[q], bytes) == cudaSuccess && cudaMalloc(&c->hf[q], bytes) == cudaSuccess;
+        ok = cudaMalloc(&c->f64.u[q], bytes) == cudaSuccess && cudaMalloc(&c->f64.hf[q], bytes) == cudaSuccess;
     }
-    ok = ok && cudaMalloc(&c->partials, kMaxPartials * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->partials, 2 * kMaxPartials * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->dsum, 4 * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->dstatus, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->hsum, 4 * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMallocHost(&c->hstatus, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_ctx(c);
@@ -210,7 +348,9 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
         set_error("stream creation failed");
         return RBGS_ECUDA;
     }
-    rbgs_status st = load_problem(c, f, u_init);
+    rbgs_status st = RBGS_OK;
+    if (c->kernel == RBGS_KERNEL_TEMPORAL) st = ensure_f64_alt(c);
+    if (st == RBGS_OK) st = load_problem(c, f, u_init);
     if (st != RBGS_OK) {
         free_ctx(c);
         return st;
@@ -223,7 +363,7 @@ rbgs_status rbgs_sweep(rbgs_t c, long nsweeps) {
     clear_error();
     if (!c) { set_error("ctx is NULL"); return RBGS_EINVAL; }
     if (nsweeps < 0) { set_error("nsweeps < 0"); return RBGS_EINVAL; }
-    if (c->g.n <= kGraphMaxN && nsweeps >= kGraphSweeps) {
+    if (c->kernel == RBGS_KERNEL_COLOUR && c->g.n <= kGraphMaxN && nsweeps >= kGraphSweeps) {
         rbgs_status st = ensure_graph(c);
         if (st != RBGS_OK) return st;
         while (nsweeps >= c->graph_sweeps) {
@@ -240,7 +380,7 @@ rbgs_status rbgs_residual(rbgs_t c, double *rel) {
     rbgs_status st = launch_residual_sum(c, c->stream);
     if (st != RBGS_OK) return st;
     RBGS_CUDA(cudaMemcpyAsync(c->hsum, c->dsum, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    RBGS_CUDA(cudaStreamSynchronize(c->stream));
+    if ((st = check_device_status(c)) != RBGS_OK) return st;
     const double r2 = c->hsum[0];
     *rel = c->den2 > 0.0 ? std::sqrt(r2) / std::sqrt(c->den2) : std::sqrt(r2);
     if (!std::isfinite(*rel)) {
@@ -254,6 +394,7 @@ rbgs_status rbgs_solve(rbgs_t c, double tol, long *sweeps_done, double *rel) {
     clear_error();
     if (!c) { set_error("ctx is NULL"); return RBGS_EINVAL; }
     if (!(tol >= 0.0)) { set_error("tol must be >= 0"); return RBGS_EINVAL; }
+    if (c->opts.precision == RBGS_FP32_REFINE) return refine_solve(c, tol, sweeps_done, rel);
     long done = 0;
     double rho = 0.0;
     rbgs_status st = rbgs_residual(c, &rho);
@@ -278,7 +419,7 @@ rbgs_status rbgs_get_solution(rbgs_t c, double *u_out) {
     if (!c || !u_out) { set_error("ctx and u_out must not be NULL"); return RBGS_EINVAL; }
     const size_t count = (size_t)c->g.rows * c->g.rows;
     if (device_accessible(u_out)) {
-        return launch_unpack_u(c->g, c->u[0], c->u[1], u_out, c->stream);
+        return launch_unpack_u(c->g, c->f64.u[0], c->f64.u[1], u_out, c->stream);
     }
     if (!c->staging) {
         if (cudaMalloc(&c->staging, count * sizeof(double)) != cudaSuccess) {
@@ -287,7 +428,7 @@ rbgs_status rbgs_get_solution(rbgs_t c, double *u_out) {
             return RBGS_ENOMEM;
         }
     }
-    rbgs_status st = launch_unpack_u(c->g, c->u[0], c->u[1], c->staging, c->stream);
+    rbgs_status st = launch_unpack_u(c->g, c->f64.u[0], c->f64.u[1], c->staging, c->stream);
     if (st != RBGS_OK) return st;
     RBGS_CUDA(cudaMemcpyAsync(u_out, c->staging, count * sizeof(double), cudaMemcpyDefault, c->stream));
     RBGS_CUDA(cudaStreamSynchronize(c->stream));

@@ -17,6 +17,7 @@
 #include <string>
 
 #include "../../include/rbgs.h"
+#include "field.cuh"
 
 namespace rbgs {
 
@@ -75,12 +76,12 @@ struct rbgs_ctx {
     cudaStream_t stream;        // caller's stream (may be 0)
     cudaStream_t capture;       // private stream used only to capture graphs
     int device;
-    // FP64 iterate and scaled right-hand side h2*f, colour-split
-    double *u[2];
-    double *hf[2];
-    // FP32 copies for the mixed-precision inner solver (allocated on demand)
-    float *d32[2];
-    float *r32[2];
+    // FP64 iterate, its temporal partner and the scaled right-hand side h2*f, colour-split
+    rbgs::ColourField<double> f64;
+    // FP32 correction (u), its partner (alt) and scaled defect (hf) of the mixed-precision
+    // refinement (allocated on first use)
+    rbgs::ColourField<float> f32;
+    int *dstatus;               // device: nonzero after a bounded wait gave up
     // natural-layout staging for host I/O (allocated on demand)
     double *staging;
     // reduction scratch and results
@@ -95,7 +96,11 @@ struct rbgs_ctx {
     int emulate;                // resolved FP64 emulation split
     int tile_rows;              // resolved rows per block
     int pts;                    // values per thread in the half-sweep (2 or 4)
-    int tblock_k;               // resolved temporal depth
+    int tblock_k;               // resolved temporal depth (FP64)
+    int tblock_k32;             // resolved temporal depth (FP32 inner sweeps)
+    int inner_sweeps;           // resolved FP32 sweeps per correction
+    int kernel32;               // resolved inner kernel for the FP32 sweeps
+    int *hstatus;               // pinned host mirror of dstatus
 };
 
 namespace rbgs {
@@ -111,6 +116,12 @@ rbgs_status launch_half_sweep(const rbgs_ctx *c, int colour, cudaStream_t s);
 rbgs_status launch_sweeps_f64(const rbgs_ctx *c, long nsweeps, cudaStream_t s);
 rbgs_status launch_residual_sum(const rbgs_ctx *c, cudaStream_t s);   // -> dsum[0]
 rbgs_status launch_rhs_norm(const rbgs_ctx *c, cudaStream_t s);       // -> dsum[1]
-rbgs_status launch_temporal_sweeps(const rbgs_ctx *c, long nsweeps, cudaStream_t s);
+rbgs_status launch_temporal_sweeps(rbgs_ctx *c, long nsweeps, cudaStream_t s);
+template <typename T>
+rbgs_status launch_temporal_pass(ColourField<T> &fld, int k, int *status, cudaStream_t s);
+rbgs_status launch_sweeps_f32(const ColourField<float> &fld, long nsweeps, cudaStream_t s);
+// mixed-precision refinement kernels (mixed.cu)
+rbgs_status launch_defect(const rbgs_ctx *c, bool write_r32, double scale, cudaStream_t s);  // -> dsum[0] sum, dsum[2] max
+rbgs_status launch_correct(const rbgs_ctx *c, double scale, cudaStream_t s);
 
 }  // namespace rbgs

@@ -9,6 +9,9 @@
 //
 // ||h^2 b|| depends only on f and the ring; it is reduced once per problem by
 // rhs_norm_kernel (h2f plus the ring neighbours of each boundary-adjacent point).
+//
+// The same walk also serves the mixed-precision refinement: max |rt| (exact, order-
+// independent) and the FP32 scaled defect (float)(rt * 2^-e) for the inner solver.
 #include "common.cuh"
 #include "sweep_impl.cuh"
 
@@ -17,11 +20,15 @@ namespace {
 
 constexpr int kFinalThreads = 1024;
 
-template <int COLOUR>
+// MAX: also reduce max |rt| (into partials[kMaxPartials + block]).  WRITE: also store
+// (float)(rt * scale) into the FP32 colour array r32 (pitch W32) at interior points: the
+// scaled defect that the mixed-precision refinement hands to its FP32 inner solver.
+template <int COLOUR, bool MAX, bool WRITE>
 __global__ void __launch_bounds__(kSweepThreads)
 residual_colour_kernel(const double *__restrict__ self, const double *__restrict__ other,
                        const double *__restrict__ hf, int n, int W, int kact,
-                       int rows_per_block, double *__restrict__ partials) {
+                       int rows_per_block, double *__restrict__ partials, float *__restrict__ r32,
+                       int W32, double scale) {
     __shared__ double red_smem[kSweepThreads / 32];
     const int lane = threadIdx.x & 31;
     const int k0 = 2 * (blockIdx.x * kSweepThreads + threadIdx.x);
@@ -29,7 +36,7 @@ residual_colour_kernel(const double *__restrict__ self, const double *__restrict
     const int i0 = 1 + blockIdx.y * rows_per_block;
     const int i1 = min(n, i0 + rows_per_block - 1);
     const double2 zero = make_double2(0.0, 0.0);
-    double acc = 0.0;
+    double acc = 0.0, mx = 0.0;
     if (i0 <= n) {
         double2 up = act ? ldg2(other + (size_t)(i0 - 1) * W + k0) : zero;
         double2 mid = act ? ldg2(other + (size_t)i0 * W + k0) : zero;
@@ -54,19 +61,38 @@ residual_colour_kernel(const double *__restrict__ self, const double *__restrict
                 double s = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(f2.x, up.x), dn.x), w0), e0);
                 double r = __dadd_rn(s, -__dmul_rn(4.0, me.x));
                 acc = __fma_rn(r, r, acc);
+                if (MAX) mx = fmax(mx, fabs(r));
+                if (WRITE) r32[(size_t)i * W32 + k0] = __double2float_rn(__dmul_rn(r, scale));
             }
             if (act && j0 + 2 <= n) {
                 double s = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(f2.y, up.y), dn.y), w1), e1);
                 double r = __dadd_rn(s, -__dmul_rn(4.0, me.y));
                 acc = __fma_rn(r, r, acc);
+                if (MAX) mx = fmax(mx, fabs(r));
+                if (WRITE) r32[(size_t)i * W32 + k0 + 1] = __double2float_rn(__dmul_rn(r, scale));
             }
             up = mid;
             mid = dn;
         }
     }
+    const size_t slot = (size_t)COLOUR * gridDim.x * gridDim.y + (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     const double t = block_sum<kSweepThreads>(acc, red_smem);
-    if (threadIdx.x == 0)
-        partials[(size_t)COLOUR * gridDim.x * gridDim.y + (size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    if (threadIdx.x == 0) partials[slot] = t;
+    if (MAX) {
+        __syncthreads();
+        const double m = block_max<kSweepThreads>(mx, red_smem);
+        if (threadIdx.x == 0) partials[kMaxPartials + slot] = m;
+    }
+}
+
+// Max of `count` partials -> *out (order-independent, exact).
+__global__ void __launch_bounds__(kFinalThreads)
+final_max_kernel(const double *__restrict__ partials, int count, double *__restrict__ out) {
+    __shared__ double smem[kFinalThreads / 32];
+    double v = 0.0;
+    for (int q = threadIdx.x; q < count; q += kFinalThreads) v = fmax(v, partials[q]);
+    const double t = block_max<kFinalThreads>(v, smem);
+    if (threadIdx.x == 0) *out = t;
 }
 
 // Sum of `count` partials in a fixed order -> *out.
@@ -114,25 +140,46 @@ int residual_rows(int n, int kact) {
 
 }  // namespace
 
-rbgs_status launch_residual_sum(const rbgs_ctx *c, cudaStream_t s) {
+namespace {
+
+template <bool MAX, bool WRITE>
+rbgs_status residual_passes(const rbgs_ctx *c, double scale, cudaStream_t s) {
     const Geometry &g = c->g;
     const int kact = active_width(g.n);
     const int rows = residual_rows(g.n, kact);
     dim3 grid((kact + 2 * kSweepThreads - 1) / (2 * kSweepThreads), (g.n + rows - 1) / rows);
-    residual_colour_kernel<0><<<grid, kSweepThreads, 0, s>>>(c->u[0], c->u[1], c->hf[0], g.n, g.W,
-                                                             kact, rows, c->partials);
+    float *r0 = WRITE ? c->f32.hf[0] : nullptr, *r1 = WRITE ? c->f32.hf[1] : nullptr;
+    residual_colour_kernel<0, MAX, WRITE><<<grid, kSweepThreads, 0, s>>>(
+        c->f64.u[0], c->f64.u[1], c->f64.hf[0], g.n, g.W, kact, rows, c->partials, r0, c->f32.W, scale);
     RBGS_LAUNCH_CHECK();
-    residual_colour_kernel<1><<<grid, kSweepThreads, 0, s>>>(c->u[1], c->u[0], c->hf[1], g.n, g.W,
-                                                             kact, rows, c->partials);
+    residual_colour_kernel<1, MAX, WRITE><<<grid, kSweepThreads, 0, s>>>(
+        c->f64.u[1], c->f64.u[0], c->f64.hf[1], g.n, g.W, kact, rows, c->partials, r1, c->f32.W, scale);
     RBGS_LAUNCH_CHECK();
-    final_sum_kernel<<<1, kFinalThreads, 0, s>>>(c->partials, 2 * (int)(grid.x * grid.y), c->dsum);
+    const int count = 2 * (int)(grid.x * grid.y);
+    final_sum_kernel<<<1, kFinalThreads, 0, s>>>(c->partials, count, c->dsum);
     RBGS_LAUNCH_CHECK();
+    if (MAX) {
+        final_max_kernel<<<1, kFinalThreads, 0, s>>>(c->partials + kMaxPartials, count, c->dsum + 2);
+        RBGS_LAUNCH_CHECK();
+    }
     return RBGS_OK;
+}
+
+}  // namespace
+
+rbgs_status launch_residual_sum(const rbgs_ctx *c, cudaStream_t s) {
+    return residual_passes<false, false>(c, 1.0, s);
+}
+
+// write_r32 = false: sum rt^2 -> dsum[0], max |rt| -> dsum[2].
+// write_r32 = true:  r32 = (float)(rt * scale) at interior points (and the sum again).
+rbgs_status launch_defect(const rbgs_ctx *c, bool write_r32, double scale, cudaStream_t s) {
+    return write_r32 ? residual_passes<false, true>(c, scale, s) : residual_passes<true, false>(c, scale, s);
 }
 
 rbgs_status launch_rhs_norm(const rbgs_ctx *c, cudaStream_t s) {
     const Geometry &g = c->g;
-    ColourPtrs u{{c->u[0], c->u[1]}}, hf{{c->hf[0], c->hf[1]}};
+    ColourPtrs u{{c->f64.u[0], c->f64.u[1]}}, hf{{c->f64.hf[0], c->f64.hf[1]}};
     size_t total = (size_t)g.n * g.n;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 1024) blocks = 1024;

@@ -86,10 +86,10 @@ rbgs_status launch_colour(const rbgs_ctx *c, int colour, cudaStream_t s) {
     const int per_block = PTS * kSweepThreads;
     dim3 grid((kact + per_block - 1) / per_block, (g.n + rows - 1) / rows);
     if (colour == 0)
-        half_sweep_f64<0, M, PLAIN, PTS><<<grid, kSweepThreads, 0, s>>>(c->u[0], c->u[1], c->hf[0],
+        half_sweep_f64<0, M, PLAIN, PTS><<<grid, kSweepThreads, 0, s>>>(c->f64.u[0], c->f64.u[1], c->f64.hf[0],
                                                                          g.n, g.W, kact, rows, 1.0);
     else
-        half_sweep_f64<1, M, PLAIN, PTS><<<grid, kSweepThreads, 0, s>>>(c->u[1], c->u[0], c->hf[1],
+        half_sweep_f64<1, M, PLAIN, PTS><<<grid, kSweepThreads, 0, s>>>(c->f64.u[1], c->f64.u[0], c->f64.hf[1],
                                                                          g.n, g.W, kact, rows, 1.0);
     RBGS_LAUNCH_CHECK();
     return RBGS_OK;

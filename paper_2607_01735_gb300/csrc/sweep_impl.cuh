@@ -70,6 +70,21 @@ __device__ __forceinline__ double block_sum(double v, double *smem) {
     return t;  // valid in thread 0
 }
 
+// Block-wide max of one non-negative double per thread.
+template <int THREADS>
+__device__ __forceinline__ double block_max(double v, double *smem) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = (lane < THREADS / 32) ? smem[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+    }
+    return t;  // valid in thread 0
+}
+
 bool emulation_split_supported(int m);
 
 }  // namespace rbgs

@@ -308,3 +308,56 @@ def test_uniform_grid_properties():
     f = synth.uniform_pm1_grid(200, 1).numpy()
     assert f.min() >= -1.0 and f.max() < 1.0
     assert abs(f.mean()) < 0.01 and abs(f.var() - 1.0 / 3.0) < 0.01
+
+
+# ---------------------------------------------------------------- mixed-precision refinement
+def test_refinement_reaches_fp64_accuracy_with_fp32_sweeps():
+    """FP32 sweeps alone stall near binary32 rounding; the FP64 defect/correction loop
+    reaches the dense direct solution to FP64-level accuracy."""
+    n = 31
+    f, u0 = _random_problem(n, 1100)
+    h2 = synth.h_squared(n)
+    exact = direct.dense_solve(f, u0, h2)
+    u = u0.copy()
+    done, rho, outer = oracle.refine_solve(u, f, h2, 1e-13, 200, 10 ** 6)
+    assert rho <= 1e-13 and outer >= 2
+    assert _relmax(u, exact) <= 1e-12
+    # plain binary32 RBGS with as many sweeps stalls at binary32 accuracy
+    u32 = u0.astype(np.float32)
+    oracle.sweeps_f32(u32, f.astype(np.float32), h2, done)
+    err32 = _relmax(u32.astype(np.float64), exact)
+    assert 1e-9 < err32 < 1e-4
+
+
+def test_refinement_converges_like_plain_rbgs():
+    """The defect equation is solved by the same iteration, so after the same number of
+    sweeps the refined residual matches plain FP64 RBGS's up to binary32 noise."""
+    n = 63
+    f, u0 = _random_problem(n, 1200, ring=True)
+    h2 = synth.h_squared(n)
+    for total in (200, 600):
+        u = u0.copy()
+        oracle.refine_solve(u, f, h2, 0.0, 100, total)
+        rho_ref, _, _ = oracle.residual(u, f, h2)
+        p = u0.copy()
+        oracle.sweeps(p, f, h2, total)
+        rho_plain = oracle.residual(p, f, h2)[0]
+        assert abs(rho_ref - rho_plain) <= 1e-5 * rho_plain
+
+
+def test_refinement_first_step_by_definition():
+    """One outer step with one inner sweep, recomputed from the definition in numpy."""
+    n = 9
+    f, u0 = _random_problem(n, 1300)
+    h2 = synth.h_squared(n)
+    u = u0.copy()
+    oracle.refine_solve(u, f, h2, 0.0, 1, 1)
+    rt = oracle.residual_field(u0, f, h2)
+    mx = np.max(np.abs(rt))
+    e = int(np.frexp(mx)[1])
+    r32 = (rt * 2.0 ** -e).astype(np.float32)
+    d = np.zeros((n + 2, n + 2), dtype=np.float32)
+    oracle.sweeps_f32(d, r32, 1.0, 1)
+    want = u0.copy()
+    want[1:-1, 1:-1] = u0[1:-1, 1:-1] + d[1:-1, 1:-1].astype(np.float64) * 2.0 ** e
+    assert np.array_equal(u, want)
