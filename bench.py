@@ -50,12 +50,19 @@ def parse():
     p.add_argument("--tile-rows", type=int, default=0)
     p.add_argument("--values", type=int, default=0, help="values per thread in a half-sweep (0 auto, 2, 4)")
     p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one launch per colour, 2 temporal")
+    p.add_argument("--tblock-k", type=int, default=0, help="sweeps per temporal pass (0 auto)")
+    p.add_argument("--precision", choices=["fp64", "refine"], default="fp64",
+                   help="fp64: plain FP64 sweeps; refine: FP32 sweeps with FP64 defect correction")
+    p.add_argument("--inner", type=int, default=0, help="FP32 sweeps per correction (refine)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
 
-def workload(n, sweeps):
+def workload(n, sweeps, precision="fp64"):
+    if precision == "refine":
+        return (f"RBGS FP32 sweeps + FP64 defect correction, {n}x{n} interior, zero Dirichlet ring, "
+                f"f~U(-1,1) seed 1, u0=0, {sweeps} sweeps + residual norm")
     return (f"plain RBGS FP64, {n}x{n} interior, zero Dirichlet ring, f~U(-1,1) seed 1, u0=0, "
             f"{sweeps} red+black sweeps + residual norm")
 
@@ -244,8 +251,11 @@ def main():
     f = synth.uniform_pm1_grid(n, 1, device=dev)
     u0 = torch.zeros(n + 2, n + 2, dtype=torch.float64, device=dev)
     out = torch.empty_like(u0)
+    refine = args.precision == "refine"
     opts = rb.default_opts(fp64_emulate=args.emulate, tile_rows=args.tile_rows, kernel=args.kernel,
-                           sweep_values=args.values)
+                           sweep_values=args.values, tblock_k=args.tblock_k,
+                           precision=rb.RBGS_FP32_REFINE if refine else rb.RBGS_FP64,
+                           inner_sweeps=args.inner, max_sweeps=sweeps)
     lib = rb.load_library()
     stream = torch.cuda.current_stream(dev)
 
@@ -262,7 +272,10 @@ def main():
         if record:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        rb.rbgs_sweep(ctx, sweeps)
+        if refine:
+            rb.rbgs_solve(ctx, 0.0, allow_not_converged=True)
+        else:
+            rb.rbgs_sweep(ctx, sweeps)
         if record:
             e1.record(stream)
             sweep_events.append((e0, e1))
@@ -271,7 +284,18 @@ def main():
         rb.rbgs_destroy(ctx)
         return rho
 
-    launches_per_step = 4 + 2 * sweeps + 3 + 1  # pack f, pack u, ||b|| (2), sweeps, residual (3), unpack
+    # pack f, pack u, ||b|| (2), the sweeps, residual (3), unpack
+    if refine:
+        inner = args.inner or 100
+        outer = -(-sweeps // inner)
+        k32 = args.tblock_k or 4
+        per_outer = 4 + 1 + 3 + (inner // k32 + 2 * (inner % k32) if (args.kernel == 2 or (args.kernel == 0 and n >= 512)) else 2 * inner)
+        launches_per_step = 4 + 4 + outer * per_outer + 3 + 1
+    elif args.kernel == 2:
+        k = args.tblock_k or 2
+        launches_per_step = 4 + sweeps // k + 2 * (sweeps % k) + 3 + 1
+    else:
+        launches_per_step = 4 + 2 * sweeps + 3 + 1
 
     for _ in range(args.warmup):
         step(f, u0, out)
@@ -293,14 +317,44 @@ def main():
     lups = float(n) * n * sweeps * args.steps * world
     value = lups / elapsed / 1e9
     sweep_s = sum(a.elapsed_time(b) for a, b in sweep_events) / 1e3
-    launch_s = sweep_s / (2 * sweeps * args.steps)
-    alg_bytes_launch = BYTES_PER_LUP * (n * n / 2.0)
-    achieved = alg_bytes_launch / launch_s / 1e9
     peaks = measured_peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
-    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
-    emulate_used = args.emulate
-    traffic = profiled_traffic(emulate_used)
+    peak_hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0)) if peaks else 2070.0
+    temporal = args.kernel == 2
+    if refine:
+        # dominant kernel: the FP32 inner half-sweep (12 algorithmic bytes per update)
+        kname = "temporal_tile<float>" if temporal or (args.kernel == 0 and n >= 512) else "half_sweep_f32"
+        per_launch_lups = n * n / 2.0
+        launch_s = sweep_s / (2 * sweeps * args.steps)  # per half-sweep equivalent
+        alg_bytes = 12 * per_launch_lups
+        achieved = alg_bytes / launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                    "frac": achieved / peak_hbm, "traffic": None, "kernel": kname, "peak_source": hbm_src,
+                    "launch_ms": 1e3 * launch_s, "algorithmic_bytes_per_launch": alg_bytes,
+                    "note": "per half-sweep equivalent, including the FP64 defect/correction passes"}
+    else:
+        # dominant kernel: the FP64 half-sweep, bound by the FP64 pipe: 4 correctly rounded
+        # adds per update (the x0.25 runs on the integer pipe).  Peak: 2 FP64 instructions
+        # per clock per SM (ncu's DFMA peak_sustained) x SMs x maximum SM clock.
+        launches = (sweeps // max(args.tblock_k or 2, 1)) if temporal else 2 * sweeps
+        kname = "temporal_tile<double>" if temporal else "half_sweep_f64"
+        per_launch_lups = n * n * sweeps / launches
+        launch_s = sweep_s / (launches * args.steps)
+        fp64_ops = 4 * per_launch_lups
+        achieved = fp64_ops / launch_s / 1e12
+        peak_alu = 2.0 * sm_count * sm_mhz * 1e6 / 1e12
+        alg_bytes = BYTES_PER_LUP * per_launch_lups
+        hbm_achieved = alg_bytes / launch_s / 1e9
+        traffic = None if temporal else profiled_traffic(args.emulate)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                    "frac": achieved / peak_alu, "traffic": traffic, "kernel": kname,
+                    "peak_source": f"FP64 pipe: 2 instr/clk/SM x {sm_count} SMs x {sm_mhz:.0f} MHz "
+                                   "(one flop = one correctly rounded FP64 add)",
+                    "launch_ms": 1e3 * launch_s, "algorithmic_bytes_per_launch": alg_bytes,
+                    "hbm": {"achieved": hbm_achieved, "peak": peak_hbm, "unit": "GB/s",
+                            "frac": hbm_achieved / peak_hbm, "peak_source": hbm_src}}
 
     e2e = None
     if not args.no_e2e:
@@ -334,19 +388,16 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 f ~ U(-1,1))",
-            "config": {"workload": workload(n, sweeps), "n": n, "sweeps": sweeps,
+            "config": {"workload": workload(n, sweeps, args.precision), "n": n, "sweeps": sweeps,
                        "kernel": "one launch per colour" if args.kernel in (0, 1) else "temporal",
-                       "fp64_emulate": emulate_used, "tile_rows": args.tile_rows or "auto",
+                       "tblock_k": args.tblock_k or "auto", "precision": args.precision,
+                       "fp64_emulate": args.emulate, "tile_rows": args.tile_rows or "auto",
                        "sweep_values": args.values or "auto",
                        "l2": "inputs larger than L2 (4 colour arrays of 1.08 GB each)",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs_algorithmic": BYTES_PER_LUP * lups / elapsed / 1e9,
             "final_rho": rho,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "half_sweep_f64", "peak_source": peak_src,
-                         "launch_ms": 1e3 * launch_s,
-                         "algorithmic_bytes_per_launch": alg_bytes_launch},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,

@@ -125,10 +125,19 @@ typedef struct {
 } rbgs_result;
 
 /*
- * Solves nprob independent problems of uneven sizes to rho <= tol each, in one
- * persistent launch.  u_out[p] receives problem p's solution ((N_p+2)^2 values); res[p]
- * its outcome.  Returns RBGS_OK when every problem converged, else the first failing
- * status.  Synchronises the stream.
+ * Solves nprob independent problems of uneven sizes (1 <= N_p <= 32768) to rho <= tol each,
+ * in one persistent launch captured with the packing and unpacking in a CUDA graph.  A
+ * thread block claims one problem at a time, largest first, and solves it on its own
+ * (FP64 sweeps with a residual check every opts->check_every sweeps, or, with
+ * RBGS_FP32_REFINE, the mixed-precision refinement with opts->inner_sweeps FP32 sweeps per
+ * correction), so each problem's iterate equals a single-problem solve with the same
+ * options.  The launch shape (threads per block, blocks per SM) is picked by a built-in
+ * autotuner on first use for a given size mix, unless opts->tile_rows (> 0: 256, 512 or
+ * 1024 threads) and opts->tblock_k (blocks per SM) fix it.  u_out[p] receives problem p's
+ * solution ((N_p+2)^2 values, device or host memory); res[p] its outcome, latency_ms
+ * measured on the device from the batch's first problem start to this problem's end.
+ * Returns RBGS_OK when every problem converged, else the first failing status.
+ * Synchronises the stream.
  */
 rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, double tol,
                                const rbgs_opts *opts, void *cuda_stream, double **u_out,

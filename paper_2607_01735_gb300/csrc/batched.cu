@@ -1,33 +1,602 @@
-// Batched solve of independent problems.
+// Batched solve of many independent Poisson problems of uneven sizes in one persistent
+// launch (rbgs_solve_batched).
+//
+// Design.  The problems are independent, so the batch shards by problem with no data
+// exchange.  A persistent grid of thread blocks (a few per SM) pulls problem indices,
+// largest first, from an atomic work counter; the block that claims a problem solves
+// it to tolerance on its own: red half-sweep, __syncthreads, black half-sweep,
+// __syncthreads (the colour phases of Algorithm 1 at block scope), a deterministic
+// block reduction of the residual every `check_every` sweeps (FP64), or the
+// mixed-precision refinement loop (FP64 defect/correction, FP32 sweeps).  No block ever
+// waits on another block, so there is nothing that can deadlock or spin.  Each problem
+// records %globaltimer stamps when its block starts and finishes it.
+//
+// The arithmetic per update is the one of the single-problem kernels (same operations,
+// same order), so every problem's iterate equals the oracle's after the same sweeps.
+// The host side packs all problems into one device pool (colour-split layout), captures
+// pack -> persistent kernel -> unpack into a CUDA graph and launches it.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
 #include "common.cuh"
+#include "sweep_impl.cuh"
+
+namespace rbgs {
+namespace {
+
+struct DevProblem {
+    int n, W, W32, pad;
+    double h2;
+    double *u[2];
+    double *hf[2];
+    float *d[2];   // FP32 correction (refinement)
+    float *r[2];   // FP32 scaled defect (refinement)
+    const double *f_nat;   // natural-layout inputs (device-readable)
+    const double *u_nat;
+    double *out_nat;       // natural-layout output (device)
+};
+
+struct DevResult {
+    int status;
+    int pad;
+    long long sweeps;
+    double rel;
+    unsigned long long t_start, t_end;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Block-wide deterministic sum/max, result broadcast to every thread.
+template <int THREADS>
+__device__ __forceinline__ double bcast_sum(double v, double *smem) {
+    const double t = block_sum<THREADS>(v, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) smem[0] = t;
+    __syncthreads();
+    const double r = smem[0];
+    __syncthreads();
+    return r;
+}
+
+template <int THREADS>
+__device__ __forceinline__ double bcast_max(double v, double *smem) {
+    const double t = block_max<THREADS>(v, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) smem[0] = t;
+    __syncthreads();
+    const double r = smem[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int kact_of(int n) { return (((n + 3) / 2) + 1) & ~1; }
+
+// One FP64 half-sweep of colour C over the whole problem by this block.  The loop trip
+// count is uniform over the block (quarter() votes across the warp).
+template <int C, int THREADS>
+__device__ void block_half_sweep_f64(const DevProblem &P) {
+    double *self = P.u[C];
+    const double *other = P.u[C ^ 1];
+    const double *hf = P.hf[C];
+    const int n = P.n, W = P.W, kact = kact_of(n), npairs = kact / 2;
+    const int items = n * npairs;
+    for (int base = 0; base < items; base += THREADS) {
+        const int q = base + threadIdx.x;
+        const bool act = q < items;
+        const int qq = act ? q : 0;
+        const int i = 1 + qq / npairs, k0 = 2 * (qq % npairs);
+        const int p = (i + C) & 1;
+        const size_t row = (size_t)i * W;
+        const double2 up = ldg2(other + row - W + k0), mid = ldg2(other + row + k0);
+        const double2 dn = ldg2(other + row + W + k0), f2 = ldg2(hf + row + k0);
+        double w0, e0, w1, e1;
+        if (p == 0) {
+            w0 = k0 > 0 ? other[row + k0 - 1] : 0.0;
+            e0 = mid.x; w1 = mid.x; e1 = mid.y;
+        } else {
+            w0 = mid.x; e0 = mid.y; w1 = mid.y;
+            e1 = (k0 + 2 < kact) ? other[row + k0 + 2] : 0.0;
+        }
+        const double r0 = update_f64<false>(0, f2.x, up.x, dn.x, w0, e0, 1.0);
+        const double r1 = update_f64<false>(0, f2.y, up.y, dn.y, w1, e1, 1.0);
+        const int j0 = 2 * k0 + p;
+        if (act && j0 >= 1 && j0 <= n) self[row + k0] = r0;
+        if (act && j0 + 2 <= n) self[row + k0 + 1] = r1;
+    }
+}
+
+// FP32 half-sweep of the defect equation (h^2 f replaced by the scaled defect r).
+template <int C, int THREADS>
+__device__ void block_half_sweep_f32(const DevProblem &P) {
+    float *self = P.d[C];
+    const float *other = P.d[C ^ 1];
+    const float *hf = P.r[C];
+    const int n = P.n, W = P.W32, kact = kact_of(n);
+    const int items = n * kact;
+    for (int base = 0; base < items; base += THREADS) {
+        const int q = base + threadIdx.x;
+        if (q < items) {
+            const int i = 1 + q / kact, k = q % kact;
+            const int j = 2 * k + ((i + C) & 1);
+            if (j >= 1 && j <= n) {
+                const size_t row = (size_t)i * W;
+                const int p = (i + C) & 1;
+                const float vw = other[row + k - 1 + p], ve = other[row + k + p];
+                float s = __fadd_rn(hf[row + k], other[row - W + k]);
+                s = __fadd_rn(s, other[row + W + k]);
+                s = __fadd_rn(s, vw);
+                s = __fadd_rn(s, ve);
+                self[row + k] = __fmul_rn(s, 0.25f);
+            }
+        }
+    }
+}
+
+// Per-thread partial of sum rt^2 (and max |rt|; optionally write (float)(rt * scale)).
+template <int THREADS, bool WRITE>
+__device__ void block_residual(const DevProblem &P, double scale, double &r2, double &mx) {
+    const int n = P.n, W = P.W, kact = kact_of(n);
+    r2 = 0.0;
+    mx = 0.0;
+    for (int c = 0; c < 2; ++c) {
+        const double *self = P.u[c], *other = P.u[c ^ 1], *hf = P.hf[c];
+        const int items = n * kact;
+        for (int q = threadIdx.x; q < items; q += THREADS) {
+            const int i = 1 + q / kact, k = q % kact;
+            const int p = (i + c) & 1;
+            const int j = 2 * k + p;
+            if (j < 1 || j > n) continue;
+            const size_t row = (size_t)i * W;
+            double s = __dadd_rn(hf[row + k], other[row - W + k]);
+            s = __dadd_rn(s, other[row + W + k]);
+            s = __dadd_rn(s, other[row + k - 1 + p]);
+            s = __dadd_rn(s, other[row + k + p]);
+            const double r = __dadd_rn(s, -__dmul_rn(4.0, self[row + k]));
+            r2 = __fma_rn(r, r, r2);
+            mx = fmax(mx, fabs(r));
+            if (WRITE) P.r[c][(size_t)i * P.W32 + k] = __double2float_rn(__dmul_rn(r, scale));
+        }
+    }
+}
+
+// sum (h^2 b)^2: h2f plus the ring neighbours, as in rhs_norm_kernel.
+template <int THREADS>
+__device__ double block_rhs_norm2(const DevProblem &P, double *smem) {
+    const int n = P.n, W = P.W;
+    double acc = 0.0;
+    const int total = n * n;
+    for (int q = threadIdx.x; q < total; q += THREADS) {
+        const int i = 1 + q / n, j = 1 + q % n;
+        auto at = [&](const double *const *a, int ii, int jj) { return a[(ii + jj) & 1][(size_t)ii * W + (jj >> 1)]; };
+        double b = at(P.hf, i, j);
+        if (i == 1) b = __dadd_rn(b, at(P.u, 0, j));
+        if (i == n) b = __dadd_rn(b, at(P.u, n + 1, j));
+        if (j == 1) b = __dadd_rn(b, at(P.u, i, 0));
+        if (j == n) b = __dadd_rn(b, at(P.u, i, n + 1));
+        acc = __fma_rn(b, b, acc);
+    }
+    return bcast_sum<THREADS>(acc, smem);
+}
+
+__device__ __forceinline__ double rho_of(double r2, double den2) {
+    return den2 > 0.0 ? sqrt(r2) / sqrt(den2) : sqrt(r2);
+}
+
+template <int THREADS>
+__device__ void solve_problem(const DevProblem &P, DevResult &R, double tol, int check_every,
+                              long long max_sweeps, int inner, bool refine, double *smem) {
+    const unsigned long long t0 = globaltimer();
+    const double den2 = block_rhs_norm2<THREADS>(P, smem);
+    double r2, mx;
+    block_residual<THREADS, false>(P, 1.0, r2, mx);
+    r2 = bcast_sum<THREADS>(r2, smem);
+    mx = bcast_max<THREADS>(mx, smem);
+    double rho = rho_of(r2, den2);
+    long long done = 0;
+    while (!(rho <= tol) && done < max_sweeps && isfinite(rho)) {
+        if (!refine) {
+            long long k = check_every;
+            if (k > max_sweeps - done) k = max_sweeps - done;
+            for (long long it = 0; it < k; ++it) {
+                block_half_sweep_f64<0, THREADS>(P);
+                __syncthreads();
+                block_half_sweep_f64<1, THREADS>(P);
+                __syncthreads();
+            }
+            done += k;
+        } else {
+            int e = 0;
+            frexp(mx, &e);
+            const double down = ldexp(1.0, -e), up = ldexp(1.0, e);
+            double t2, tm;
+            block_residual<THREADS, true>(P, down, t2, tm);  // writes the scaled defect
+            const size_t elems = (size_t)(P.n + 2) * P.W32;
+            for (size_t q = threadIdx.x; q < elems; q += THREADS) {
+                P.d[0][q] = 0.0f;
+                P.d[1][q] = 0.0f;
+            }
+            __syncthreads();
+            long long k = inner;
+            if (k > max_sweeps - done) k = max_sweeps - done;
+            for (long long it = 0; it < k; ++it) {
+                block_half_sweep_f32<0, THREADS>(P);
+                __syncthreads();
+                block_half_sweep_f32<1, THREADS>(P);
+                __syncthreads();
+            }
+            // u += (double)d * 2^e at interior points
+            const int n = P.n, kact = kact_of(n);
+            for (int c = 0; c < 2; ++c) {
+                for (int q = threadIdx.x; q < n * kact; q += THREADS) {
+                    const int i = 1 + q / kact, kk = q % kact;
+                    const int j = 2 * kk + ((i + c) & 1);
+                    if (j < 1 || j > n) continue;
+                    double &uu = P.u[c][(size_t)i * P.W + kk];
+                    uu = __dadd_rn(uu, __dmul_rn((double)P.d[c][(size_t)i * P.W32 + kk], up));
+                }
+            }
+            __syncthreads();
+            done += k;
+        }
+        block_residual<THREADS, false>(P, 1.0, r2, mx);
+        r2 = bcast_sum<THREADS>(r2, smem);
+        mx = bcast_max<THREADS>(mx, smem);
+        rho = rho_of(r2, den2);
+    }
+    if (threadIdx.x == 0) {
+        R.status = !isfinite(rho) ? RBGS_ENONFINITE : (rho <= tol ? RBGS_OK : RBGS_ENOTCONV);
+        R.sweeps = done;
+        R.rel = rho;
+        R.t_start = t0;
+        R.t_end = globaltimer();
+    }
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+batched_persistent_kernel(const DevProblem *__restrict__ probs, DevResult *__restrict__ res,
+                          const int *__restrict__ order, int nprob, int *queue, double tol,
+                          int check_every, long long max_sweeps, int inner, int refine) {
+    __shared__ double smem[THREADS / 32 + 1];
+    __shared__ int s_q;
+    for (;;) {
+        if (threadIdx.x == 0) s_q = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = s_q;
+        __syncthreads();
+        if (q >= nprob) break;
+        const int p = order[q];
+        const DevProblem P = probs[p];
+        solve_problem<THREADS>(P, res[p], tol, check_every, max_sweeps, inner, refine != 0, smem);
+        __syncthreads();
+    }
+}
+
+// Pack every problem's natural-layout inputs into its colour-split arrays (blockIdx.z =
+// problem) and unpack the solutions afterwards.
+__global__ void batch_pack_kernel(const DevProblem *__restrict__ probs) {
+    const DevProblem P = probs[blockIdx.z];
+    const int n = P.n, W = P.W, ld = n + 2;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= W) return;
+    for (int i = blockIdx.y; i < n + 2; i += gridDim.y) {
+        const int j = 2 * k;
+        const double a = (j <= n + 1) ? P.u_nat[(size_t)i * ld + j] : 0.0;
+        const double b = (j + 1 <= n + 1) ? P.u_nat[(size_t)i * ld + j + 1] : 0.0;
+        double *ev = (i & 1) ? P.u[1] : P.u[0];
+        double *od = (i & 1) ? P.u[0] : P.u[1];
+        ev[(size_t)i * W + k] = a;
+        od[(size_t)i * W + k] = b;
+        const bool row_in = i >= 1 && i <= n;
+        const double fa = (row_in && j >= 1 && j <= n) ? __dmul_rn(P.h2, P.f_nat[(size_t)(i - 1) * n + (j - 1)]) : 0.0;
+        const double fb = (row_in && j + 1 <= n) ? __dmul_rn(P.h2, P.f_nat[(size_t)(i - 1) * n + j]) : 0.0;
+        double *fev = (i & 1) ? P.hf[1] : P.hf[0];
+        double *fod = (i & 1) ? P.hf[0] : P.hf[1];
+        fev[(size_t)i * W + k] = fa;
+        fod[(size_t)i * W + k] = fb;
+    }
+}
+
+__global__ void batch_unpack_kernel(const DevProblem *__restrict__ probs) {
+    const DevProblem P = probs[blockIdx.z];
+    const int n = P.n, W = P.W, ld = n + 2;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = 2 * k;
+    if (j > n + 1) return;
+    for (int i = blockIdx.y; i < n + 2; i += gridDim.y) {
+        const double *ev = (i & 1) ? P.u[1] : P.u[0];
+        const double *od = (i & 1) ? P.u[0] : P.u[1];
+        P.out_nat[(size_t)i * ld + j] = ev[(size_t)i * W + k];
+        if (j + 1 <= n + 1) P.out_nat[(size_t)i * ld + j + 1] = od[(size_t)i * W + k];
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+bool device_readable(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct LaunchConfig {
+    int threads;       // 256, 512 or 1024
+    int blocks_per_sm;
+};
+
+rbgs_status launch_persistent(const LaunchConfig &lc, int sms, DevProblem *d_probs, DevResult *d_res,
+                              int *d_order, int nprob, int *d_queue, double tol, int check_every,
+                              long long max_sweeps, int inner, int refine, cudaStream_t s) {
+    RBGS_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
+    const int grid = std::max(1, std::min(nprob, sms * lc.blocks_per_sm));
+    switch (lc.threads) {
+    case 256:
+        batched_persistent_kernel<256><<<grid, 256, 0, s>>>(d_probs, d_res, d_order, nprob, d_queue, tol,
+                                                            check_every, max_sweeps, inner, refine);
+        break;
+    case 512:
+        batched_persistent_kernel<512><<<grid, 512, 0, s>>>(d_probs, d_res, d_order, nprob, d_queue, tol,
+                                                            check_every, max_sweeps, inner, refine);
+        break;
+    default:
+        batched_persistent_kernel<1024><<<grid, 1024, 0, s>>>(d_probs, d_res, d_order, nprob, d_queue, tol,
+                                                              check_every, max_sweeps, inner, refine);
+        break;
+    }
+    RBGS_LAUNCH_CHECK();
+    return RBGS_OK;
+}
+
+// Autotuner: block size and blocks per SM for the persistent kernel.  Neither changes a
+// result bit; each candidate runs a few sweeps of the real batch (after which the
+// problems are re-packed), the fastest per update wins.  Cached per process by
+// (device, precision, sizes).
+struct TuneKey {
+    int device, refine;
+    std::vector<int> sizes;
+    bool operator==(const TuneKey &o) const { return device == o.device && refine == o.refine && sizes == o.sizes; }
+};
+std::mutex g_tune_mutex;
+std::vector<std::pair<TuneKey, LaunchConfig>> g_tune_cache;
+
+}  // namespace
+}  // namespace rbgs
+
+using namespace rbgs;
 
 extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, double tol,
-                                          const rbgs_opts *opts, void *cuda_stream,
-                                          double **u_out, rbgs_result *res) {
-    rbgs::clear_error();
+                                          const rbgs_opts *opts, void *cuda_stream, double **u_out,
+                                          rbgs_result *res) {
+    clear_error();
     if (nprob < 0 || (nprob > 0 && (!probs || !u_out || !res))) {
-        rbgs::set_error("bad batched arguments");
+        set_error("bad batched arguments");
         return RBGS_EINVAL;
     }
-    rbgs_status first = RBGS_OK;
-    for (int p = 0; p < nprob; ++p) {
-        rbgs_t c = nullptr;
-        rbgs_status st = rbgs_create(probs[p].n, probs[p].h2, probs[p].f, probs[p].u_init, opts,
-                                     cuda_stream, &c);
-        long sweeps = 0;
-        double rel = NAN;
-        if (st == RBGS_OK) st = rbgs_solve(c, tol, &sweeps, &rel);
-        if (st == RBGS_OK || st == RBGS_ENOTCONV) {
-            rbgs_status g = rbgs_get_solution(c, u_out[p]);
-            if (g != RBGS_OK) st = g;
-        }
-        rbgs_destroy(c);
-        res[p].status = st;
-        res[p].sweeps = sweeps;
-        res[p].rel = rel;
-        res[p].latency_ms = 0.0;
-        if (st != RBGS_OK && first == RBGS_OK) first = st;
+    if (!(tol >= 0.0)) { set_error("tol must be >= 0"); return RBGS_EINVAL; }
+    if (nprob == 0) return RBGS_OK;
+    rbgs_opts o;
+    rbgs_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.check_every <= 0) o.check_every = 100;
+    if (o.max_sweeps <= 0) o.max_sweeps = 1000000000L;
+    const int inner = o.inner_sweeps > 0 ? o.inner_sweeps : 100;
+    const int refine = o.precision == RBGS_FP32_REFINE ? 1 : 0;
+    if (o.precision != RBGS_FP64 && o.precision != RBGS_FP32_REFINE) {
+        set_error("unknown precision %d", o.precision);
+        return RBGS_EINVAL;
     }
+    for (int p = 0; p < nprob; ++p) {
+        if (probs[p].n < 1 || probs[p].n > 32768 || !(probs[p].h2 > 0.0) || !probs[p].f || !probs[p].u_init || !u_out[p]) {
+            set_error("problem %d: n must be in 1..32768, h2 > 0, pointers non-NULL", p);
+            return RBGS_EINVAL;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int device = 0, sms = 0;
+    RBGS_CUDA(cudaGetDevice(&device));
+    RBGS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+
+    // ---- device pool: colour-split state per problem + natural staging where needed
+    std::vector<DevProblem> hp(nprob);
+    std::vector<size_t> off_u(nprob), off_nat_f(nprob), off_nat_u(nprob), off_out(nprob);
+    size_t total = 0;
+    for (int p = 0; p < nprob; ++p) {
+        const int n = probs[p].n;
+        const int W = colour_width(n), W32 = colour_width_bytes(n, 4);
+        const size_t c64 = align256((size_t)(n + 2) * W * sizeof(double));
+        const size_t c32 = align256((size_t)(n + 2) * W32 * sizeof(float));
+        off_u[p] = total;
+        total += 4 * c64 + (refine ? 4 * c32 : 0);
+        const size_t natf = align256((size_t)n * n * sizeof(double));
+        const size_t natu = align256((size_t)(n + 2) * (n + 2) * sizeof(double));
+        off_nat_f[p] = device_readable(probs[p].f) ? (size_t)-1 : (total += natf, total - natf);
+        off_nat_u[p] = device_readable(probs[p].u_init) ? (size_t)-1 : (total += natu, total - natu);
+        off_out[p] = device_readable(u_out[p]) ? (size_t)-1 : (total += natu, total - natu);
+        hp[p].n = n;
+        hp[p].W = W;
+        hp[p].W32 = W32;
+        hp[p].h2 = probs[p].h2;
+    }
+    char *pool = nullptr;
+    if (cudaMalloc(&pool, total) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("batched pool allocation of %zu bytes failed", total);
+        return RBGS_ENOMEM;
+    }
+    DevProblem *d_probs = nullptr;
+    DevResult *d_res = nullptr;
+    int *d_order = nullptr, *d_queue = nullptr;
+    rbgs_status st = RBGS_OK;
+    auto fail_cuda = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && st == RBGS_OK) {
+            set_error("%s: %s", what, cudaGetErrorString(e));
+            st = RBGS_ECUDA;
+        }
+    };
+    fail_cuda(cudaMalloc(&d_probs, nprob * sizeof(DevProblem)), "cudaMalloc");
+    fail_cuda(cudaMalloc(&d_res, nprob * sizeof(DevResult)), "cudaMalloc");
+    fail_cuda(cudaMalloc(&d_order, nprob * sizeof(int)), "cudaMalloc");
+    fail_cuda(cudaMalloc(&d_queue, sizeof(int)), "cudaMalloc");
+    if (st == RBGS_OK) fail_cuda(cudaMemsetAsync(pool, 0, total, s), "cudaMemsetAsync");
+    for (int p = 0; p < nprob && st == RBGS_OK; ++p) {
+        const int n = probs[p].n;
+        const size_t c64 = align256((size_t)(n + 2) * hp[p].W * sizeof(double));
+        const size_t c32 = align256((size_t)(n + 2) * hp[p].W32 * sizeof(float));
+        char *b = pool + off_u[p];
+        hp[p].u[0] = (double *)b;
+        hp[p].u[1] = (double *)(b + c64);
+        hp[p].hf[0] = (double *)(b + 2 * c64);
+        hp[p].hf[1] = (double *)(b + 3 * c64);
+        hp[p].d[0] = refine ? (float *)(b + 4 * c64) : nullptr;
+        hp[p].d[1] = refine ? (float *)(b + 4 * c64 + c32) : nullptr;
+        hp[p].r[0] = refine ? (float *)(b + 4 * c64 + 2 * c32) : nullptr;
+        hp[p].r[1] = refine ? (float *)(b + 4 * c64 + 3 * c32) : nullptr;
+        if (off_nat_f[p] == (size_t)-1) {
+            hp[p].f_nat = probs[p].f;
+        } else {
+            hp[p].f_nat = (const double *)(pool + off_nat_f[p]);
+            fail_cuda(cudaMemcpyAsync(pool + off_nat_f[p], probs[p].f, (size_t)n * n * sizeof(double),
+                                      cudaMemcpyDefault, s), "cudaMemcpyAsync");
+        }
+        if (off_nat_u[p] == (size_t)-1) {
+            hp[p].u_nat = probs[p].u_init;
+        } else {
+            hp[p].u_nat = (const double *)(pool + off_nat_u[p]);
+            fail_cuda(cudaMemcpyAsync(pool + off_nat_u[p], probs[p].u_init, (size_t)(n + 2) * (n + 2) * sizeof(double),
+                                      cudaMemcpyDefault, s), "cudaMemcpyAsync");
+        }
+        hp[p].out_nat = off_out[p] == (size_t)-1 ? u_out[p] : (double *)(pool + off_out[p]);
+    }
+    // largest problems first (longest-processing-time order balances the blocks)
+    std::vector<int> order(nprob);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return probs[a].n > probs[b].n; });
+    int maxW = 0, maxRows = 0;
+    for (int p = 0; p < nprob; ++p) {
+        maxW = std::max(maxW, hp[p].W);
+        maxRows = std::max(maxRows, hp[p].n + 2);
+    }
+    if (st == RBGS_OK) fail_cuda(cudaMemcpyAsync(d_probs, hp.data(), nprob * sizeof(DevProblem), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+    if (st == RBGS_OK) fail_cuda(cudaMemcpyAsync(d_order, order.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
+    const dim3 pgrid((maxW + 255) / 256, std::min(maxRows, 64), nprob);
+
+    // ---- autotune the launch shape (per process, per device/precision/size mix)
+    LaunchConfig lc{1024, 1};
+    if (st == RBGS_OK && nprob > 65535) { set_error("at most 65535 problems per batch"); st = RBGS_EINVAL; }
+    if (st == RBGS_OK) {
+        TuneKey key{device, refine, {}};
+        for (int p = 0; p < nprob; ++p) key.sizes.push_back(probs[p].n);
+        std::sort(key.sizes.begin(), key.sizes.end());
+        bool found = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            for (auto &e : g_tune_cache)
+                if (e.first == key) { lc = e.second; found = true; }
+        }
+        const bool tune = o.tile_rows == 0 && !found;
+        if (o.tile_rows > 0) {
+            // explicit request: tile_rows selects the block size, tblock_k the blocks per SM
+            lc.threads = o.tile_rows >= 1024 ? 1024 : (o.tile_rows >= 512 ? 512 : 256);
+            lc.blocks_per_sm = o.tblock_k > 0 ? o.tblock_k : 1;
+        }
+        if (tune) {
+            const LaunchConfig cands[] = {{1024, 1}, {512, 2}, {512, 1}, {256, 4}, {256, 2}};
+            cudaEvent_t e0, e1;
+            fail_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+            fail_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+            float best = 1e30f;
+            const long long probe = refine ? std::min<long long>(inner, 20) : 20;
+            for (const LaunchConfig &cand : cands) {
+                if (st != RBGS_OK) break;
+                batch_pack_kernel<<<pgrid, 256, 0, s>>>(d_probs);
+                fail_cuda(cudaGetLastError(), "pack launch");
+                fail_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
+                // tol < 0 is never reached: every problem runs exactly `probe` sweeps
+                if (st == RBGS_OK)
+                    st = launch_persistent(cand, sms, d_probs, d_res, d_order, nprob, d_queue, -1.0,
+                                           (int)probe, probe, (int)probe, refine, s);
+                fail_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
+                fail_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+                float ms = 0.f;
+                fail_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+                if (st == RBGS_OK && ms < best) {
+                    best = ms;
+                    lc = cand;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (st == RBGS_OK) {
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                g_tune_cache.push_back({key, lc});
+            }
+        }
+    }
+
+    // ---- the batch: pack -> persistent solve -> unpack, captured as one CUDA graph
+    if (st == RBGS_OK) {
+        cudaStream_t cap = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        fail_cuda(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate");
+        if (st == RBGS_OK) fail_cuda(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "capture");
+        if (st == RBGS_OK) {
+            batch_pack_kernel<<<pgrid, 256, 0, cap>>>(d_probs);
+            fail_cuda(cudaGetLastError(), "pack launch");
+            rbgs_status ls = launch_persistent(lc, sms, d_probs, d_res, d_order, nprob, d_queue, tol,
+                                               o.check_every, o.max_sweeps, inner, refine, cap);
+            if (ls != RBGS_OK && st == RBGS_OK) st = ls;
+            batch_unpack_kernel<<<pgrid, 256, 0, cap>>>(d_probs);
+            fail_cuda(cudaGetLastError(), "unpack launch");
+            cudaError_t e = cudaStreamEndCapture(cap, &graph);
+            fail_cuda(e, "end capture");
+        }
+        if (st == RBGS_OK) fail_cuda(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+        if (st == RBGS_OK) fail_cuda(cudaGraphLaunch(exec, s), "graph launch");
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+    }
+    // ---- results and host outputs
+    std::vector<DevResult> hr(nprob);
+    if (st == RBGS_OK) fail_cuda(cudaMemcpyAsync(hr.data(), d_res, nprob * sizeof(DevResult), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync");
+    for (int p = 0; p < nprob && st == RBGS_OK; ++p) {
+        if (off_out[p] != (size_t)-1)
+            fail_cuda(cudaMemcpyAsync(u_out[p], pool + off_out[p], (size_t)(probs[p].n + 2) * (probs[p].n + 2) * sizeof(double),
+                                      cudaMemcpyDefault, s), "cudaMemcpyAsync");
+    }
+    fail_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    rbgs_status first = st;
+    if (st == RBGS_OK) {
+        unsigned long long t_begin = ~0ull;
+        for (int p = 0; p < nprob; ++p) t_begin = std::min(t_begin, hr[p].t_start);
+        for (int p = 0; p < nprob; ++p) {
+            res[p].status = hr[p].status;
+            res[p].sweeps = (long)hr[p].sweeps;
+            res[p].rel = hr[p].rel;
+            res[p].latency_ms = (double)(hr[p].t_end - t_begin) * 1e-6;
+            if (hr[p].status != RBGS_OK && first == RBGS_OK) {
+                first = (rbgs_status)hr[p].status;
+                set_error("problem %d: status %d after %lld sweeps (rho = %.3e)", p, hr[p].status,
+                          hr[p].sweeps, hr[p].rel);
+            }
+        }
+    }
+    cudaFree(pool);
+    cudaFree(d_probs);
+    cudaFree(d_res);
+    cudaFree(d_order);
+    cudaFree(d_queue);
     return first;
 }

@@ -1,0 +1,124 @@
+"""GPU parity for rbgs_solve_batched: many uneven problems in one persistent launch.
+
+Every problem's solution must equal the oracle's single-problem solve with the same
+options bit for bit (FP64: residual check every check_every sweeps; FP32 refinement:
+inner sweeps per correction), with the same sweep count, whatever launch shape the
+autotuner or the caller picks.  Where the oracle's rho and the GPU's rho (different
+summation order) straddle the tolerance the sweep counts may legitimately differ by one
+check interval; the test inputs keep clear of that, and the check is still that the
+rho values agree to 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2607_01735_gb300 as rb
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_01735_gb300 import build
+    build.build_library()
+    rb.load_library()
+
+
+def _batch(sizes, seed):
+    out = []
+    for p, n in enumerate(sizes):
+        f = synth.uniform_pm1_grid(n, seed * 1000 + p).numpy().copy()
+        c = float(synth.uniform01(seed * 1000 + 500 + p, 1).numpy()[0] * 2 - 1)
+        u = np.zeros((n + 2, n + 2))
+        u[0, :] = u[-1, :] = u[:, 0] = u[:, -1] = c
+        out.append((n, synth.h_squared(n), f, u))
+    return out
+
+
+def _assert_bits(got, ref):
+    if not np.array_equal(got.view(np.uint64), ref.view(np.uint64)):
+        bad = np.argwhere(got.view(np.uint64) != ref.view(np.uint64))
+        raise AssertionError(f"{len(bad)} values differ; first at {tuple(bad[0])}")
+
+
+def _run(batch, tol, device=True, **opts):
+    o = rb.default_opts(**opts)
+    if device:
+        probs = [(n, h2, torch.from_numpy(f).cuda(), torch.from_numpy(u).cuda()) for n, h2, f, u in batch]
+        outs = [torch.empty((n + 2, n + 2), dtype=torch.float64, device="cuda") for n, _, _, _ in batch]
+    else:
+        probs = [(n, h2, f, u) for n, h2, f, u in batch]
+        outs = [np.empty((n + 2, n + 2)) for n, _, _, _ in batch]
+    res = rb.rbgs_solve_batched(probs, tol, outs, o, allow_failures=True)
+    outs = [x.cpu().numpy() if isinstance(x, torch.Tensor) else x for x in outs]
+    return res, outs
+
+
+SIZES = [1, 2, 5, 31, 33, 63, 64, 100, 127, 40, 7, 63]
+
+
+@pytest.mark.parametrize("shape", [(0, 0), (256, 2), (512, 1), (1024, 1)])
+def test_batched_fp64_matches_oracle(shape):
+    batch = _batch(SIZES, 3)
+    threads, per_sm = shape
+    res, outs = _run(batch, 1e-8, check_every=25, tile_rows=threads, tblock_k=per_sm)
+    for (n, h2, f, u0), r, got in zip(batch, res, outs):
+        ref = u0.copy()
+        done, rho = oracle.solve(ref, f, h2, 1e-8, 25, 10 ** 7)
+        assert r["status"] == rb.RBGS_OK
+        assert r["sweeps"] == done, (n, r["sweeps"], done)
+        assert abs(r["rel"] - rho) <= 1e-12 * max(rho, 1e-300)
+        _assert_bits(got, ref)
+        assert r["latency_ms"] >= 0.0
+
+
+def test_batched_refinement_matches_oracle():
+    batch = _batch([63, 31, 100, 5, 127], 4)
+    res, outs = _run(batch, 1e-9, precision=rb.RBGS_FP32_REFINE, inner_sweeps=40)
+    for (n, h2, f, u0), r, got in zip(batch, res, outs):
+        ref = u0.copy()
+        done, rho, _ = oracle.refine_solve(ref, f, h2, 1e-9, 40, 10 ** 7)
+        assert r["status"] == rb.RBGS_OK and r["sweeps"] == done
+        assert abs(r["rel"] - rho) <= 1e-12 * rho
+        _assert_bits(got, ref)
+
+
+def test_batched_host_buffers_and_not_converged():
+    batch = _batch([20, 9, 33], 5)
+    res, outs = _run(batch, 1e-14, device=False, check_every=10, max_sweeps=30)
+    for (n, h2, f, u0), r, got in zip(batch, res, outs):
+        ref = u0.copy()
+        oracle.sweeps(ref, f, h2, 30)
+        assert r["status"] == rb.RBGS_ENOTCONV and r["sweeps"] == 30
+        _assert_bits(got, ref)
+    with pytest.raises(rb.RbgsError) as e:
+        rb.rbgs_solve_batched([(p[0], p[1], p[2], p[3]) for p in batch], 1e-14,
+                              [np.empty((p[0] + 2, p[0] + 2)) for p in batch],
+                              rb.default_opts(check_every=10, max_sweeps=30))
+    assert e.value.status == rb.RBGS_ENOTCONV
+
+
+@pytest.mark.slow
+def test_batched_512_uneven_problems_sampled():
+    """512 problems with the batched workload's recipe (size index and boundary constant
+    from stream 3, f from stream 3*2^16+p), sizes restricted to {63, 127} so that the
+    whole batch reaches 1e-8 in seconds; 8 problems re-solved by the oracle."""
+    table = synth.batched_problem_table(512, 3, sizes=(63, 127))
+    batch = []
+    for e in table:
+        f, u, h2 = synth.batched_problem(e)
+        batch.append((e["n"], h2, f, u))
+    res, outs = _run(batch, 1e-8, check_every=100)
+    assert all(r["status"] == rb.RBGS_OK and r["rel"] <= 1e-8 for r in res)
+    lat = np.array([r["latency_ms"] for r in res])
+    assert np.all(lat > 0)
+    for p in [0, 1, 100, 255, 256, 400, 510, 511]:
+        n, h2, f, u0 = batch[p]
+        ref = u0.copy()
+        done, rho = oracle.solve(ref, f, h2, 1e-8, 100, 10 ** 7)
+        assert res[p]["sweeps"] == done
+        _assert_bits(outs[p], ref)
