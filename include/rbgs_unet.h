@@ -1,0 +1,97 @@
+/*
+ * rbgs_unet.h -- C ABI of the learned initial guess in librbgs.so.
+ *
+ * The paper has no counterpart: a small convolutional U-Net maps a Poisson problem's
+ * right-hand side and Dirichlet data to an initial guess u0 for red-black Gauss-Seidel,
+ * which then runs to the same tolerance as from u0 = 0 (so RBGS remains both the
+ * fallback and the judge of the network's error).
+ *
+ * Tensors are NHWC (channels fastest), batch B, height H, width W.  Activations and
+ * operands of the convolutions are bfloat16 (uint16_t bit patterns); accumulation is
+ * FP32; master weights, gradients and Adam moments are FP32.  All pointers are device
+ * memory of the current device unless stated otherwise.  Work is ordered on the given
+ * stream (a cudaStream_t; NULL = legacy default stream).  Status codes are rbgs_status.
+ *
+ * Network (4 levels, base width 32): per level two 3x3 convolutions with ReLU, 2x2
+ * average pooling down, nearest-neighbour upsampling up, skip connections by channel
+ * concatenation, widths 32/64/128/256, a final 1x1 convolution to one channel.  Input
+ * channels: f, boundary mask (1 on the Dirichlet ring), boundary values g (0 off the
+ * ring), zero-padded to 16 channels internally.  H and W must be multiples of 8.
+ */
+#ifndef RBGS_UNET_H
+#define RBGS_UNET_H
+
+#include <stdint.h>
+
+#include "rbgs.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- layer kernels --- */
+
+/*
+ * 3x3 convolution, stride 1, zero padding 1 (cross-correlation, as in deep learning):
+ *   Y[b,y,x,o] = act( bias[o] + sum_{dy,dx,c} Wt[o,dy,dx,c] * X[b,y+dy-1,x+dx-1,c] )
+ * X: B*H*W*Cin bf16; Wt: Cout*3*3*Cin bf16; bias: Cout fp32 (may be NULL);
+ * Y: B*H*W*Cout bf16, or fp32 when y_fp32 != 0.  act = ReLU when relu != 0.
+ * Cin and Cout must be multiples of 8.  ksize is 3 (or 1 for a 1x1 convolution).
+ */
+rbgs_status rbgs_conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y,
+                              int B, int H, int W, int Cin, int Cout, int ksize, int relu,
+                              int y_fp32, void *cuda_stream);
+
+/*
+ * Backward of rbgs_conv_forward without the activation, given G = dLoss/d(pre-activation)
+ * (B*H*W*Cout bf16):
+ *   dX[b,y,x,c]  (+)= sum_{dy,dx,o} Wt[o,dy,dx,c] * G[b,y-dy+1,x-dx+1,o]   (fp32; added to
+ *                     the existing contents when accumulate != 0; dX may be NULL)
+ *   dW[o,dy,dx,c] += sum_{b,y,x} G[b,y,x,o] * X[b,y+dy-1,x+dx-1,c]       (fp32, accumulated)
+ *   db[o]        += sum_{b,y,x} G[b,y,x,o]                                (fp32; may be NULL)
+ * Wt_t is scratch of 9*Cin*Cout bf16 (device) used for the transposed weights.
+ */
+rbgs_status rbgs_conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t *G, float *dX,
+                               float *dW, float *db, uint16_t *Wt_t, int B, int H, int W, int Cin,
+                               int Cout, int ksize, int accumulate, void *cuda_stream);
+
+/* -------------------------------------------------------------------- network --- */
+
+typedef struct rbgs_unet *rbgs_unet_t;
+
+/* Creates the network with weights initialised from `seed` (He-uniform, SplitMix64). */
+rbgs_status rbgs_unet_create(uint64_t seed, void *cuda_stream, rbgs_unet_t *out);
+
+/* Number of FP32 parameters (weights and biases of all layers, in a fixed order). */
+long rbgs_unet_num_params(rbgs_unet_t net);
+
+/* Copies the FP32 master parameters to / from `params` (host or device memory). */
+rbgs_status rbgs_unet_get_params(rbgs_unet_t net, float *params);
+rbgs_status rbgs_unet_set_params(rbgs_unet_t net, const float *params);
+
+/*
+ * Forward pass: x is B*H*W*3 fp32 (f, mask, g), y receives B*H*W fp32 predictions.
+ * Buffers for B x H x W are allocated on first use and reused.
+ */
+rbgs_status rbgs_unet_forward(rbgs_unet_t net, const float *x, float *y, int B, int H, int W);
+
+/*
+ * One training step: forward, loss = sum(mask_loss * (y - target)^2) / sum(mask_loss),
+ * backward (every layer by the library's kernels), one Adam update (lr, beta1 0.9, beta2
+ * 0.999, eps 1e-8) of the FP32 master weights, which are then rounded to bf16 for the
+ * next forward.  mask_loss is B*H*W fp32 (1 where the loss counts).  *loss receives the
+ * loss before the update (synchronises the stream).  When grads != NULL the step stops
+ * after the backward pass (no update) and copies the FP32 gradient, in parameter order,
+ * to grads (num_params values, host or device).
+ */
+rbgs_status rbgs_unet_train_step(rbgs_unet_t net, const float *x, const float *target,
+                                 const float *mask_loss, int B, int H, int W, float lr,
+                                 float *loss, float *grads);
+
+void rbgs_unet_destroy(rbgs_unet_t net);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBGS_UNET_H */

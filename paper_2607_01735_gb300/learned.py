@@ -1,0 +1,107 @@
+"""Learned initial guess: data generation by the solver itself, training, application.
+
+Workflow (the growth direction in which a network proposes u0 and red-black
+Gauss-Seidel finishes to the same tolerance):
+  1. `make_dataset`: Gaussian-random-field right-hand sides and random linear Dirichlet
+     data (synth.learned_guess_sample), solved to a tight tolerance by
+     rbgs_solve_batched (one persistent launch); inputs (f, ring mask, ring values) and
+     targets (the converged grids) stay on the GPU.
+  2. `train`: minibatch Adam steps, each one rbgs_unet_train_step (forward, backward and
+     update in the library's kernels).
+  3. `initial_guess`: the network's prediction with the Dirichlet ring restored; for a
+     grid finer than the training grid, `initial_guess_coarse` predicts on the training
+     resolution (f block-averaged, ring sampled) and interpolates bilinearly.
+The solver then runs from that u0 to the requested tolerance, exactly as from u0 = 0.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+from . import default_opts, rbgs_solve_batched, RBGS_FP64
+from .unet import UNet, network_input
+
+
+def grid_size(n: int) -> int:
+    return (n + 2 + 7) // 8 * 8
+
+
+def make_dataset(n: int, streams, tol: float = 1e-12, device="cuda", batch: int = 512):
+    """(x, target, mask) on the device for problems drawn from `streams` at size n."""
+    import synth
+    size = grid_size(n)
+    xs, ys = [], []
+    streams = list(streams)
+    h2 = synth.h_squared(n)
+    opts = default_opts(precision=RBGS_FP64, check_every=200)
+    for start in range(0, len(streams), batch):
+        chunk = streams[start:start + batch]
+        probs, outs, rings = [], [], []
+        for s in chunk:
+            f, u = synth.learned_guess_sample(n, s)
+            fd, ud = torch.from_numpy(f).to(device), torch.from_numpy(u).to(device)
+            probs.append((n, h2, fd, ud))
+            outs.append(torch.empty_like(ud))
+            rings.append(ud)
+        res = rbgs_solve_batched(probs, tol, outs, opts)
+        for (nn, _, fd, ud), sol in zip(probs, outs):
+            xs.append(network_input(fd, ud, size))
+            t = torch.zeros((size, size), dtype=torch.float32, device=device)
+            t[:n + 2, :n + 2] = sol.to(torch.float32)
+            ys.append(t)
+    x = torch.stack(xs)
+    y = torch.stack(ys)
+    mask = torch.zeros((size, size), dtype=torch.float32, device=device)
+    mask[1:n + 1, 1:n + 1] = 1.0
+    return x, y, mask.expand(x.shape[0], size, size).contiguous()
+
+
+def train(net: UNet, x, y, mask, steps: int, batch: int = 16, lr: float = 1e-3, seed: int = 0,
+          log_every: int = 0):
+    """Adam minibatch training; returns the list of losses."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    losses = []
+    nsamp = x.shape[0]
+    for it in range(steps):
+        idx = torch.randint(0, nsamp, (batch,), generator=g).to(x.device)
+        step_lr = lr * (0.5 * (1 + np.cos(np.pi * it / max(steps, 1))))  # cosine decay
+        losses.append(net.train_step(x[idx].contiguous(), y[idx].contiguous(), mask[idx].contiguous(), step_lr))
+        if log_every and it % log_every == 0:
+            print(f"step {it} loss {losses[-1]:.4e}", flush=True)
+    return losses
+
+
+def initial_guess(net: UNet, f: torch.Tensor, u_ring: torch.Tensor) -> torch.Tensor:
+    """u0 on the (n+2)^2 grid: the network's interior prediction, the given Dirichlet ring."""
+    n = f.shape[0]
+    size = grid_size(n)
+    x = network_input(f, u_ring, size).unsqueeze(0)
+    pred = net.forward(x)[0]
+    u0 = u_ring.clone().to(torch.float64)
+    u0[1:n + 1, 1:n + 1] = pred[1:n + 1, 1:n + 1].to(torch.float64)
+    return u0
+
+
+def initial_guess_coarse(net: UNet, f: torch.Tensor, u_ring: torch.Tensor, n_coarse: int) -> torch.Tensor:
+    """Predict on an n_coarse grid (f averaged, ring sampled) and interpolate bilinearly to
+    the fine grid; the fine Dirichlet ring is kept.  (n + 1) must be a multiple of
+    (n_coarse + 1) so that coarse nodes coincide with fine nodes."""
+    n = f.shape[0]
+    r = (n + 1) // (n_coarse + 1)
+    if r * (n_coarse + 1) != n + 1:
+        raise ValueError("(n + 1) must be a multiple of (n_coarse + 1)")
+    # f at coarse interior nodes: average of the fine nodes around each coarse node
+    fpad = torch.zeros((n + 2, n + 2), dtype=torch.float64, device=f.device)
+    fpad[1:n + 1, 1:n + 1] = f
+    k = 2 * r - 1
+    avg = F.avg_pool2d(fpad[None, None], kernel_size=k, stride=1, padding=r - 1)[0, 0]
+    idx = torch.arange(1, n_coarse + 1, device=f.device) * r
+    fc = avg[idx][:, idx]
+    ring_idx = torch.arange(0, n_coarse + 2, device=f.device) * r
+    uc_ring = u_ring[ring_idx][:, ring_idx].clone()
+    uc = initial_guess(net, fc, uc_ring)
+    fine = F.interpolate(uc[None, None], size=(n + 2, n + 2), mode="bilinear", align_corners=True)[0, 0]
+    u0 = u_ring.clone().to(torch.float64)
+    u0[1:n + 1, 1:n + 1] = fine[1:n + 1, 1:n + 1]
+    return u0

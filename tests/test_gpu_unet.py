@@ -1,0 +1,132 @@
+"""GPU parity for the learned initial guess: the library's convolution kernels and the
+whole network's gradient against the float64 oracle, training, and what the trained
+network gains over starting red-black Gauss-Seidel from u0 = 0.
+
+Operands are bf16 on the GPU, so the oracle receives the same bf16-rounded inputs;
+single-layer results then differ only by FP32 accumulation order (tolerance 1e-4 of
+the result scale).  The whole network stores bf16 activations between layers, so its
+gradient is compared by direction (cosine >= 0.99) and norm (within 5%).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2607_01735_gb300 as rb
+import synth
+from oracle import unet_ref as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_01735_gb300 import build
+    build.build_library()
+    rb.load_library()
+
+
+def _bf(a):
+    return torch.from_numpy(a).to(torch.float32).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout,k", [(2, 8, 8, 16, 32, 3), (1, 13, 11, 32, 64, 3), (2, 16, 16, 96, 32, 3),
+                                              (3, 9, 7, 32, 8, 1), (1, 33, 40, 384, 128, 3)])
+def test_conv_forward_and_backward_match_oracle(B, H, W, Cin, Cout, k):
+    from paper_2607_01735_gb300 import unet as un
+    rng = np.random.default_rng(Cin + Cout + k)
+    x = _bf(rng.normal(size=(B, H, W, Cin)))
+    w = _bf(rng.normal(size=(Cout, k, k, Cin)) / np.sqrt(k * k * Cin))
+    bias = torch.from_numpy(rng.normal(size=Cout).astype(np.float32))
+    g = _bf(rng.normal(size=(B, H, W, Cout)))
+    xd, wd, bd, gd = x.cuda(), w.cuda(), bias.cuda(), g.cuda()
+    y = torch.empty((B, H, W, Cout), dtype=torch.float32, device="cuda")
+    un.rbgs_conv_forward(xd, wd, bd, y, relu=False)
+    dx = torch.empty((B, H, W, Cin), dtype=torch.float32, device="cuda")
+    dw = torch.zeros((Cout, k, k, Cin), dtype=torch.float32, device="cuda")
+    db = torch.zeros(Cout, dtype=torch.float32, device="cuda")
+    un.rbgs_conv_backward(xd, wd, gd, dx, dw, db)
+    torch.cuda.synchronize()
+    X, Wn, G = (t.to(torch.float64).numpy() for t in (x.float(), w.float(), g.float()))
+    y_ref = U.conv_forward(X, Wn, bias.double().numpy())
+    dx_ref, dw_ref, db_ref = U.conv_backward(X, Wn, G)
+    for got, ref in ((y, y_ref), (dx, dx_ref), (dw, dw_ref), (db, db_ref)):
+        got = got.cpu().double().numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref)) + 1e-6
+    # ReLU and bf16 output of the forward
+    yb = torch.empty((B, H, W, Cout), dtype=torch.bfloat16, device="cuda")
+    un.rbgs_conv_forward(xd, wd, bd, yb, relu=True)
+    ref = np.maximum(y_ref, 0)
+    assert np.max(np.abs(yb.float().cpu().numpy() - ref)) <= 1e-2 * np.max(np.abs(ref))
+
+
+def test_network_gradient_matches_oracle():
+    from paper_2607_01735_gb300.unet import UNet
+    net = UNet(seed=7)
+    params = net.get_params().cpu().double().numpy()
+    rng = np.random.default_rng(5)
+    B, H, W = 2, 16, 16
+    x3 = rng.normal(size=(B, H, W, 3))
+    target = rng.normal(size=(B, H, W)) * 0.1
+    mask = (rng.uniform(size=(B, H, W)) > 0.2).astype(np.float64)
+    # the GPU's forward consumes bf16 weights and inputs: give the oracle the same values
+    pb = torch.from_numpy(params).float().to(torch.bfloat16).double().numpy()
+    xb = torch.from_numpy(x3).float().to(torch.bfloat16).double().numpy()
+    L_ref, g_ref = U.backward(pb, xb, target, mask)
+    grads = torch.empty(net.num_params, dtype=torch.float32, device="cuda")
+    L = net.train_step(torch.from_numpy(x3).float().cuda(), torch.from_numpy(target).float().cuda(),
+                       torch.from_numpy(mask).float().cuda(), lr=0.0, grads=grads)
+    g = grads.cpu().double().numpy()
+    assert abs(L - L_ref) <= 2e-2 * L_ref
+    cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
+    assert cos >= 0.99, cos
+    assert abs(np.linalg.norm(g) / np.linalg.norm(g_ref) - 1) <= 0.05
+    # padded input channels carry no gradient
+    sl, _ = U.param_slices()
+    w0 = g[sl[0][0]].reshape(32, 3, 3, 16)
+    assert np.all(w0[..., 3:] == 0)
+
+
+def test_training_reduces_loss_and_forward_matches_oracle():
+    from paper_2607_01735_gb300.unet import UNet
+    net = UNet(seed=1)
+    rng = np.random.default_rng(9)
+    B, H, W = 4, 16, 16
+    x = torch.from_numpy(rng.normal(size=(B, H, W, 3))).float().cuda()
+    t = torch.from_numpy(np.sin(rng.normal(size=(B, H, W)))).float().cuda() * 0.2
+    m = torch.ones((B, H, W), device="cuda")
+    losses = [net.train_step(x, t, m, lr=3e-3) for _ in range(150)]
+    assert losses[-1] < 0.3 * losses[0]
+    # forward of the trained net vs the oracle on the same (bf16-rounded) parameters
+    p = net.get_params().cpu().float().to(torch.bfloat16).double().numpy()
+    y = net.forward(x).cpu().double().numpy()
+    y_ref = U.forward(p, x.cpu().float().to(torch.bfloat16).double().numpy())[..., 0]
+    assert np.max(np.abs(y - y_ref)) <= 5e-2 * np.max(np.abs(y_ref))
+
+
+@pytest.mark.slow
+def test_learned_guess_saves_sweeps():
+    """Train on 384 solver-generated solutions (31^2, GRF f, linear boundary), then solve 8
+    held-out problems to 1e-8 from u0 = 0 and from the network's guess (same solver,
+    same tolerance): the guess must need fewer sweeps."""
+    from paper_2607_01735_gb300 import learned
+    from paper_2607_01735_gb300.unet import UNet
+    n = 31
+    x, y, m = learned.make_dataset(n, range(10, 10 + 384), tol=1e-11)
+    net = UNet(seed=3)
+    losses = learned.train(net, x, y, m, steps=600, batch=16, lr=2e-3)
+    assert losses[-1] < 0.1 * losses[0]
+    h2 = synth.h_squared(n)
+    saved = []
+    for s in range(5000, 5008):
+        f, u = synth.learned_guess_sample(n, s)
+        fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u).cuda()
+        u0 = learned.initial_guess(net, fd, ud)
+        with rb.Solver(n, h2, fd, ud, check_every=10) as sol:
+            base, _, _ = sol.solve(1e-8)
+        with rb.Solver(n, h2, fd, u0.contiguous(), check_every=10) as sol:
+            warm, _, _ = sol.solve(1e-8)
+        saved.append(base - warm)
+    assert np.mean(saved) > 0, saved
