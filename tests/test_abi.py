@@ -11,6 +11,8 @@ import paper_2607_01735_gb300 as rb
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "rbgs.h")
+HEADERS = sorted(os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include"))
+                 if h.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -20,10 +22,10 @@ def lib():
     return rb.load_library()
 
 
-def _declared():
-    text = open(HEADER).read()
+def _declared(path=HEADER):
+    text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(rbgs_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(rbgs_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_binding_names():
@@ -31,13 +33,16 @@ def test_header_declares_the_binding_names():
 
 
 def test_library_exports_every_declared_symbol(lib):
-    for name in _declared():
-        assert hasattr(lib, name), name
-    # and the shared object really exports them (dynamic symbol table)
     import subprocess
     out = subprocess.run(["nm", "-D", "--defined-only", rb.LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r" T (rbgs_\w+)", out))
-    assert set(_declared()) <= exported
+    assert len(HEADERS) >= 2
+    for h in HEADERS:
+        names = _declared(h)
+        assert names, h
+        for name in names:
+            assert hasattr(lib, name), name
+        assert set(names) <= exported, (h, set(names) - exported)
 
 
 def test_default_opts(lib):
