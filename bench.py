@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -54,7 +55,12 @@ def parse():
     p.add_argument("--precision", choices=["fp64", "refine"], default="fp64",
                    help="fp64: plain FP64 sweeps; refine: FP32 sweeps with FP64 defect correction")
     p.add_argument("--inner", type=int, default=0, help="FP32 sweeps per correction (refine)")
-    p.add_argument("--mode", choices=["grid", "batched"], default="grid",
+    p.add_argument("--train-samples", type=int, default=4096, help="learned: training problems (255^2)")
+    p.add_argument("--train-steps", type=int, default=3000, help="learned: Adam steps")
+    p.add_argument("--eval-sizes", default="1023,4095", help="learned: held-out grid sizes")
+    p.add_argument("--eval-fields", type=int, default=2, help="learned: held-out fields per size")
+    p.add_argument("--eval-cap", default="2500000,400000", help="learned: sweep cap per solve, per size")
+    p.add_argument("--mode", choices=["grid", "batched", "learned"], default="grid",
                    help="grid: one large grid (default); batched: many uneven problems in one launch")
     p.add_argument("--nprob", type=int, default=512)
     p.add_argument("--sizes", default="63,127,255,511,1023", help="batched: allowed interior sizes")
@@ -304,12 +310,100 @@ def run_batched(args):
     return 0
 
 
+def _solve_from(rb, n, h2, f, u0, tol, cap, chunk):
+    """Mixed-precision solve from u0 in chunks of `chunk` sweeps up to `cap`; returns
+    (sweeps, rho, seconds, extrapolated sweeps to tol or None)."""
+    import torch
+    opts = rb.default_opts(precision=rb.RBGS_FP32_REFINE, inner_sweeps=200, max_sweeps=chunk)
+    t0 = time.perf_counter()
+    hist = []
+    done, rho = 0, None
+    with rb.Solver(n, h2, f, u0, opts) as s:
+        while done < cap:
+            d, rho, st = s.solve(tol, allow_not_converged=True)
+            done += d
+            hist.append((done, rho))
+            if st == rb.RBGS_OK or d == 0:
+                break
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    extra = None
+    if rho > tol and len(hist) >= 2 and hist[-1][1] < hist[-2][1]:
+        (s0, r0), (s1, r1) = hist[-2], hist[-1]
+        rate = math.log(r1 / r0) / (s1 - s0)
+        extra = int(s1 + math.log(tol / r1) / rate)
+    return done, rho, secs, extra
+
+
+def run_learned(args):
+    """Train the U-Net on solver-generated 255^2 solutions, then solve held-out GRF
+    problems at larger sizes to args.tol from u0 = 0 and from the network's guess
+    (predicted at the training resolution and interpolated, and predicted at full
+    resolution); reports sweeps and wall time per start."""
+    import torch
+
+    import paper_2607_01735_gb300 as rb
+    import synth
+    from paper_2607_01735_gb300 import learned
+    from paper_2607_01735_gb300.unet import UNet
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    x, y, m = learned.make_dataset(255, range(10, 10 + args.train_samples), tol=1e-12, refine=True)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = UNet(seed=0)
+    t0 = time.perf_counter()
+    losses = learned.train(net, x, y, m, steps=args.train_steps, batch=16, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del x, y, m
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    torch.save(net.get_params().cpu(), os.path.join(ROOT, "gpurun_out", "unet_params.pt"))
+    results = []
+    caps = [int(v) for v in args.eval_cap.split(",")]
+    for si, n in enumerate(int(v) for v in args.eval_sizes.split(",")):
+        cap = caps[min(si, len(caps) - 1)]
+        h2 = synth.h_squared(n)
+        for k in range(args.eval_fields):
+            stream = 5000 + 100 * k + n % 97
+            f, u = synth.learned_guess_sample(n, stream)
+            fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u).cuda()
+            row = {"n": n, "stream": stream}
+            for name in ("zero", "coarse", "full"):
+                t1 = time.perf_counter()
+                if name == "zero":
+                    u0 = ud
+                elif name == "coarse":
+                    u0 = learned.initial_guess_coarse(net, fd, ud, 255).contiguous()
+                else:
+                    u0 = learned.initial_guess(net, fd, ud).contiguous()
+                torch.cuda.synchronize()
+                t_guess = time.perf_counter() - t1
+                sweeps, rho, secs, extra = _solve_from(rb, n, h2, fd, u0, args.tol, cap, 20000)
+                row[name] = {"sweeps": sweeps, "rho": rho, "solve_s": secs, "guess_s": t_guess,
+                             "sweeps_to_tol_extrapolated": extra}
+            results.append(row)
+    line = {"metric": "sweeps and wall time to relative residual %.0e from the learned guess vs u0=0" % args.tol,
+            "value": None, "unit": "sweeps", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": f"U-Net (4 levels, 32 base channels, bf16 weights, fp32 accum) trained on "
+                                   f"{args.train_samples} RBGS solutions at 255^2 (GRF |k|^-3, linear boundary), "
+                                   f"{args.train_steps} Adam steps; held-out GRF fields at {args.eval_sizes}; "
+                                   f"solver: FP32 sweeps + FP64 refinement"},
+            "train": {"data_s": t_data, "train_s": t_train, "loss_first": losses[0], "loss_last": losses[-1],
+                      "loss_min": min(losses)},
+            "results": results}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "batched":
         return run_batched(args)
+    if args.mode == "learned":
+        return run_learned(args)
     import torch
     import torch.distributed as dist
 

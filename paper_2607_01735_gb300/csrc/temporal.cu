@@ -52,7 +52,7 @@ cudaError_t encode_tensor_map_2d(CUtensorMap *map, const void *base, int elem_by
 
 namespace {
 
-constexpr int kTThreads = 256;
+constexpr int kTThreads = 1024;
 constexpr uint32_t kWaitPolls = 1u << 22;  // bounded mbarrier wait
 
 template <typename T, int K, int TR, int TK>
@@ -68,6 +68,7 @@ struct TCfg {
     static_assert(EK <= 256 && ER <= 256, "TMA box dimensions are limited to 256");
     static_assert((EK * sizeof(T)) % 16 == 0, "TMA box rows must be whole 16-byte units");
     static_assert(TK % ALIGN == 0, "tile x origin must be 16-byte aligned");
+    static_assert(EK % 32 == 0 && kTThreads % EK == 0, "row bands must hold whole warps");
 };
 
 template <typename T>
@@ -131,33 +132,45 @@ temporal_tile(const __grid_constant__ CUtensorMap mu0, const __grid_constant__ C
         return;
     }
 
+    // Half-step s of colour c updates the points at distance > s from the region's edge.
+    // Thread t owns column kk = t % EK and marches down band t / EK of the step's rows,
+    // keeping the other colour's rows i-1, i, i+1 in registers; the horizontal neighbour
+    // that is not in its own column comes from the adjacent lane (or, at a warp edge,
+    // from shared memory).  Bands hold whole warps, so every loop below is warp-uniform.
+    constexpr int BANDS = kTThreads / C::EK;
+    const int kk = threadIdx.x % C::EK, band = threadIdx.x / C::EK;
+    const int lane = threadIdx.x & 31;
     for (int s = 0; s < 2 * K; ++s) {
         const int c = s & 1;
         T *const self = c ? su1 : su0;
         const T *const oth = c ? su0 : su1;
         const T *const fh = c ? sf1 : sf0;
-        const int rows_s = C::ER - 2 * (s + 1);
-        const int total = rows_s * C::EK;
-        for (int b = 0; b < total; b += kTThreads) {
-            const int idx = b + threadIdx.x;
-            bool valid = idx < total;
-            const int ii = s + 1 + (valid ? idx / C::EK : 0);
-            const int kk = valid ? idx % C::EK : 1;
-            const int i = R0 + ii;
-            const int p = (i + c) & 1;  // column offset of colour c in row i (two's complement)
-            const int jj = 2 * kk + p;  // natural column relative to the region's first column
-            valid = valid && jj >= s + 1 && (2 * C::EK - 1 - jj) >= s + 1;
-            const int j = 2 * E0 + jj;
-            valid = valid && i >= 1 && i <= n && j >= 1 && j <= n;
-            int kw = kk - 1 + p, ke = kk + p;
-            kw = kw < 0 ? 0 : kw;
-            ke = ke > C::EK - 1 ? C::EK - 1 : ke;
-            const T vn = oth[(ii - 1) * C::EK + kk];
-            const T vs = oth[(ii + 1) * C::EK + kk];
-            const T vw = oth[ii * C::EK + kw];
-            const T ve = oth[ii * C::EK + ke];
-            const T r = Update<T>::go(fh[ii * C::EK + kk], vn, vs, vw, ve, one);
-            if (valid) self[ii * C::EK + kk] = r;
+        const int rlo = s + 1, rhi = C::ER - 1 - s;  // rows [rlo, rhi)
+        const int per = (rhi - rlo + BANDS - 1) / BANDS;
+        const int r0 = rlo + band * per;
+        const int r1 = r0 + per < rhi ? r0 + per : rhi;
+        if (r0 < r1) {
+            T up = oth[(r0 - 1) * C::EK + kk];
+            T mid = oth[r0 * C::EK + kk];
+            for (int ii = r0; ii < r1; ++ii) {
+                const T dn = oth[(ii + 1) * C::EK + kk];
+                const T fv = fh[ii * C::EK + kk];
+                const int i = R0 + ii;
+                const int p = (i + c) & 1;  // column offset of colour c in row i
+                T prev = __shfl_up_sync(0xffffffffu, mid, 1);
+                T next = __shfl_down_sync(0xffffffffu, mid, 1);
+                if (lane == 0) prev = kk > 0 ? oth[ii * C::EK + kk - 1] : T(0);
+                if (lane == 31) next = kk + 1 < C::EK ? oth[ii * C::EK + kk + 1] : T(0);
+                const T vw = p ? mid : prev, ve = p ? next : mid;
+                const T r = Update<T>::go(fv, up, dn, vw, ve, one);
+                const int jj = 2 * kk + p;  // natural column relative to the region's first column
+                const int j = 2 * E0 + jj;
+                const bool valid = jj >= s + 1 && (2 * C::EK - 1 - jj) >= s + 1 && i >= 1 && i <= n &&
+                                   j >= 1 && j <= n;
+                if (valid) self[ii * C::EK + kk] = r;
+                up = mid;
+                mid = dn;
+            }
         }
         __syncthreads();
     }
@@ -221,20 +234,20 @@ rbgs_status run_pass(ColourField<T> &fld, int *status, cudaStream_t s) {
 
 template <>
 rbgs_status launch_temporal_pass<double>(ColourField<double> &fld, int k, int *status, cudaStream_t s) {
-    switch (k) {
-    case 1: return run_pass<double, 1, 32, 64>(fld, status, s);
-    case 2: return run_pass<double, 2, 32, 64>(fld, status, s);
-    case 4: return run_pass<double, 4, 32, 64>(fld, status, s);
+    switch (k) {  // tiles of 32 rows x (64 - 2 HK) values: EK = 64 = one quarter of the block
+    case 1: return run_pass<double, 1, 32, 60>(fld, status, s);
+    case 2: return run_pass<double, 2, 32, 56>(fld, status, s);
+    case 4: return run_pass<double, 4, 32, 52>(fld, status, s);
     default: set_error("FP64 temporal depth must be 1, 2 or 4 (got %d)", k); return RBGS_EINVAL;
     }
 }
 
 template <>
 rbgs_status launch_temporal_pass<float>(ColourField<float> &fld, int k, int *status, cudaStream_t s) {
-    switch (k) {
-    case 2: return run_pass<float, 2, 32, 128>(fld, status, s);
-    case 4: return run_pass<float, 4, 32, 128>(fld, status, s);
-    case 8: return run_pass<float, 8, 32, 128>(fld, status, s);
+    switch (k) {  // tiles of 32 rows x (128 - 2 HK) values: EK = 128 = half of the block
+    case 2: return run_pass<float, 2, 32, 120>(fld, status, s);
+    case 4: return run_pass<float, 4, 32, 112>(fld, status, s);
+    case 8: return run_pass<float, 8, 32, 104>(fld, status, s);
     default: set_error("FP32 temporal depth must be 2, 4 or 8 (got %d)", k); return RBGS_EINVAL;
     }
 }

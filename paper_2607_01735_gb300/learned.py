@@ -19,7 +19,7 @@ import numpy as np
 import torch
 import torch.nn.functional as F
 
-from . import default_opts, rbgs_solve_batched, RBGS_FP64
+from . import default_opts, rbgs_solve_batched, RBGS_FP64, RBGS_FP32_REFINE
 from .unet import UNet, network_input
 
 
@@ -27,14 +27,17 @@ def grid_size(n: int) -> int:
     return (n + 2 + 7) // 8 * 8
 
 
-def make_dataset(n: int, streams, tol: float = 1e-12, device="cuda", batch: int = 512):
-    """(x, target, mask) on the device for problems drawn from `streams` at size n."""
+def make_dataset(n: int, streams, tol: float = 1e-12, device="cuda", batch: int = 512, refine: bool = False):
+    """(x, target, mask) on the device for problems drawn from `streams` at size n,
+    targets solved by rbgs_solve_batched (FP64 sweeps, or FP32 sweeps with FP64
+    refinement when `refine`)."""
     import synth
     size = grid_size(n)
     xs, ys = [], []
     streams = list(streams)
     h2 = synth.h_squared(n)
-    opts = default_opts(precision=RBGS_FP64, check_every=200)
+    opts = default_opts(precision=RBGS_FP32_REFINE if refine else RBGS_FP64, check_every=200,
+                        inner_sweeps=400)
     for start in range(0, len(streams), batch):
         chunk = streams[start:start + batch]
         probs, outs, rings = [], [], []
