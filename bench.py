@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--emulate", type=int, default=-1, help="FP64 add split (-1: library default)")
     p.add_argument("--tile-rows", type=int, default=0)
     p.add_argument("--values", type=int, default=0, help="values per thread in a half-sweep (0 auto, 2, 4)")
+    p.add_argument("--rows", type=int, default=0, help="rows per loop step in a half-sweep (0 auto, 1, 2)")
     p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one launch per colour, 2 temporal")
     p.add_argument("--tblock-k", type=int, default=0, help="sweeps per temporal pass (0 auto)")
     p.add_argument("--precision", choices=["fp64", "refine"], default="fp64",
@@ -67,6 +68,8 @@ def parse():
     p.add_argument("--tol", type=float, default=1e-8, help="batched: relative residual target")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-ttr", action="store_true", help="skip the time-to-residual comparison")
+    p.add_argument("--ttr-n", type=int, default=511, help="grid for the time-to-residual comparison")
     return p.parse_args()
 
 
@@ -203,6 +206,29 @@ def cpu_oracle_rate(n, stream=1, target_s=10.0):
     return {"value": n * n * done / elapsed / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} sweep(s) of the {n}x{n} grid (plain single-threaded C, -O2 "
                       f"-ffp-contract=off), {elapsed:.1f} s"}
+
+
+def time_to_residual(n, tol=1e-8, stream=0):
+    """Wall time to relative residual `tol` from u0 = 0 (f ~ U(-1,1), zero ring): plain
+    FP64 RBGS vs FP32 sweeps with FP64 defect correction, same GPU, same check interval."""
+    import torch
+
+    import paper_2607_01735_gb300 as rb
+    import synth
+    h2 = synth.h_squared(n)
+    f = synth.uniform_pm1_grid(n, stream, device="cuda")
+    u0 = torch.zeros(n + 2, n + 2, dtype=torch.float64, device="cuda")
+    out = {"n": n, "tol": tol, "workload": f"{n}x{n}, f~U(-1,1) stream {stream}, zero ring, u0=0"}
+    for name, kw in (("plain_fp64", dict(check_every=100)),
+                     ("fp32_refine", dict(precision=rb.RBGS_FP32_REFINE, inner_sweeps=100))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with rb.Solver(n, h2, f, u0, **kw) as s:
+            sweeps, rho, st = s.solve(tol, allow_not_converged=True)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "sweeps": sweeps, "rho": rho, "status": st}
+    out["speedup"] = out["plain_fp64"]["seconds"] / out["fp32_refine"]["seconds"]
+    return out
 
 
 def run_reference(args):
@@ -422,7 +448,7 @@ def main():
     out = torch.empty_like(u0)
     refine = args.precision == "refine"
     opts = rb.default_opts(fp64_emulate=args.emulate, tile_rows=args.tile_rows, kernel=args.kernel,
-                           sweep_values=args.values, tblock_k=args.tblock_k,
+                           sweep_values=args.values, sweep_rows=args.rows, tblock_k=args.tblock_k,
                            precision=rb.RBGS_FP32_REFINE if refine else rb.RBGS_FP64,
                            inner_sweeps=args.inner, max_sweeps=sweeps)
     lib = rb.load_library()
@@ -552,6 +578,7 @@ def main():
         cpu = None
         if not args.no_cpu_baseline:
             cpu = cpu_oracle_rate(n)
+        ttr = None if args.no_ttr else time_to_residual(args.ttr_n)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -561,7 +588,7 @@ def main():
                        "kernel": "one launch per colour" if args.kernel in (0, 1) else "temporal",
                        "tblock_k": args.tblock_k or "auto", "precision": args.precision,
                        "fp64_emulate": args.emulate, "tile_rows": args.tile_rows or "auto",
-                       "sweep_values": args.values or "auto",
+                       "sweep_values": args.values or "auto", "sweep_rows": args.rows or "auto",
                        "l2": "inputs larger than L2 (4 colour arrays of 1.08 GB each)",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs_algorithmic": BYTES_PER_LUP * lups / elapsed / 1e9,
@@ -571,6 +598,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks.summary(),
+            "time_to_residual": ttr,
         }
         print(json.dumps(line))
     if world > 1:

@@ -69,6 +69,7 @@ typedef struct {
     int fp64_emulate;  /* FP64 adds issued on the integer pipe per 8 (-1: automatic)       */
     int inner_sweeps;  /* FP32 sweeps per defect correction for RBGS_FP32_REFINE (0: auto) */
     int sweep_values;  /* values each thread updates per row in a half-sweep: 2 or 4 (0: auto) */
+    int sweep_rows;    /* rows each thread updates per loop step in a half-sweep: 1 or 2 (0: auto) */
 } rbgs_opts;
 
 /* Fills *opts with the defaults (all automatic). */

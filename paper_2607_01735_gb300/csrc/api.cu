@@ -81,6 +81,7 @@ rbgs_status load_problem(rbgs_ctx *c, const double *f, const double *u_init) {
 void free_ctx(rbgs_ctx *c) {
     if (!c) return;
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph32) cudaGraphExecDestroy(c->graph32);
     for (int q = 0; q < 2; ++q) {
         cudaFree(c->f64.u[q]);
         cudaFree(c->f64.hf[q]);
@@ -198,6 +199,32 @@ rbgs_status defect_stats(rbgs_ctx *c, double *rho, double *mx) {
 }
 
 rbgs_status inner_sweeps_f32(rbgs_ctx *c, long m) {
+    // full inner blocks of one-launch-per-colour sweeps on small grids: a cached graph
+    if (c->kernel32 == RBGS_KERNEL_COLOUR && m == c->inner_sweeps && c->g.n <= kGraphMaxN) {
+        if (!c->graph32) {
+            cudaGraph_t graph = nullptr;
+            RBGS_CUDA(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+            rbgs_status st = launch_sweeps_f32(c->f32, m, c->capture);
+            cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
+            if (st != RBGS_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (e != cudaSuccess) {
+                set_error("graph capture failed: %s", cudaGetErrorString(e));
+                return RBGS_ECUDA;
+            }
+            e = cudaGraphInstantiate(&c->graph32, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                c->graph32 = nullptr;
+                set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+                return RBGS_ECUDA;
+            }
+        }
+        RBGS_CUDA(cudaGraphLaunch(c->graph32, c->stream));
+        return RBGS_OK;
+    }
     if (c->kernel32 == RBGS_KERNEL_TEMPORAL) {
         const int k = c->tblock_k32;
         const long passes = m / k;
@@ -290,6 +317,9 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     if (o.sweep_values != 0 && o.sweep_values != 2 && o.sweep_values != 4) {
         set_error("sweep_values must be 0, 2 or 4"); return RBGS_EINVAL;
     }
+    if (o.sweep_rows != 0 && o.sweep_rows != 1 && o.sweep_rows != 2) {
+        set_error("sweep_rows must be 0, 1 or 2"); return RBGS_EINVAL;
+    }
     if (o.tile_rows < 0 || o.tblock_k < 0 || o.inner_sweeps < 0) {
         set_error("negative tile_rows / tblock_k / inner_sweeps"); return RBGS_EINVAL;
     }
@@ -311,6 +341,7 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     c->tile_rows = o.tile_rows ? o.tile_rows : 32;
     if (c->tile_rows < (n + 65534) / 65535) c->tile_rows = (n + 65534) / 65535;  // grid.y limit
     c->pts = o.sweep_values ? o.sweep_values : 2;
+    c->sweep_rows = o.sweep_rows ? o.sweep_rows : 1;
     // FP64 sweeps: temporal depth (used when kernel == TEMPORAL)
     c->tblock_k = (o.precision == RBGS_FP64 && o.tblock_k) ? o.tblock_k : 2;
     // FP32 inner sweeps of the refinement: temporal tiles for large grids unless told otherwise

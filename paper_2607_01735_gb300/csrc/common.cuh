@@ -92,10 +92,12 @@ struct rbgs_ctx {
     // cached graph of `graph_sweeps` sweeps
     cudaGraphExec_t graph;
     long graph_sweeps;
+    cudaGraphExec_t graph32;    // cached graph of inner_sweeps FP32 sweeps (refinement)
     int kernel;                 // resolved rbgs_kernel
     int emulate;                // resolved FP64 emulation split
     int tile_rows;              // resolved rows per block
     int pts;                    // values per thread in the half-sweep (2 or 4)
+    int sweep_rows;             // rows per loop step in the half-sweep (1 or 2)
     int tblock_k;               // resolved temporal depth (FP64)
     int tblock_k32;             // resolved temporal depth (FP32 inner sweeps)
     int inner_sweeps;           // resolved FP32 sweeps per correction

@@ -3,7 +3,7 @@
 //
 // Work decomposition.  A thread owns PTS (2 or 4) neighbouring values k0.. of its colour
 // in a row, loaded and stored as 16-byte vectors, and walks down `rows` consecutive
-// rows of a strip.  The other colour's rows i-1, i, i+1 live in registers as the strip
+// rows of a strip, one or two rows per loop step.  The other colour's rows i-1, i, i+1 live in registers as the strip
 // advances, so every value of the other colour is loaded from memory once per strip
 // (plus the two rows shared with neighbouring strips), h2*f once, and the own colour is
 // only written: 24 bytes of DRAM traffic per point update in FP64.  The west/east
@@ -22,54 +22,84 @@
 namespace rbgs {
 namespace {
 
-// PTS values per thread (2 or 4): more values give the FP64 pipe more independent
-// update chains per thread.
+// PTS values per thread (2 or 4) and ROWS rows per loop step (1 or 2): both give the FP64
+// pipe more independent update chains per thread (all updates of one colour are
+// independent of each other).
 template <int COLOUR, int M, bool PLAIN, int PTS>
+__device__ __forceinline__ void update_row(double *__restrict__ self, const double *__restrict__ other,
+                                           const double *up, const double *mid, const double *dn,
+                                           const double *f, int i, int k0, int n, int W, int kact, bool act,
+                                           int lane, double one) {
+    const size_t row = (size_t)i * W;
+    const int p = (i + COLOUR) & 1;  // column offset of this colour in row i
+    double r[PTS];
+    if (p == 0) {
+        // value q sits at natural column 2(k0+q): west = other[k0+q-1], east = other[k0+q]
+        double prev = __shfl_up_sync(0xffffffffu, mid[PTS - 1], 1);
+        if (lane == 0) prev = (act && k0 > 0) ? __ldg(other + row + k0 - 1) : 0.0;
+#pragma unroll
+        for (int q = 0; q < PTS; ++q)
+            r[q] = update_f64<PLAIN>((M >> (4 * (q & 1))) & 15, f[q], up[q], dn[q], q ? mid[q - 1] : prev, mid[q],
+                                     one);
+    } else {
+        // value q sits at 2(k0+q)+1: west = other[k0+q], east = other[k0+q+1]
+        double next = __shfl_down_sync(0xffffffffu, mid[0], 1);
+        if (lane == 31) next = (k0 + PTS < kact) ? __ldg(other + row + k0 + PTS) : 0.0;
+#pragma unroll
+        for (int q = 0; q < PTS; ++q)
+            r[q] = update_f64<PLAIN>((M >> (4 * (q & 1))) & 15, f[q], up[q], dn[q], mid[q],
+                                     q + 1 < PTS ? mid[q + 1] : next, one);
+    }
+    const int j0 = 2 * k0 + p;  // natural column of value 0; value q is at j0 + 2q
+    double *sp = self + row + k0;
+    if (act && j0 >= 1 && j0 + 2 * (PTS - 1) <= n) {
+        store_row<PTS>(sp, r);
+    } else if (act) {
+#pragma unroll
+        for (int q = 0; q < PTS; ++q)
+            if (j0 + 2 * q >= 1 && j0 + 2 * q <= n) sp[q] = r[q];
+    }
+}
+
+template <int COLOUR, int M, bool PLAIN, int PTS, int ROWS>
 __global__ void __launch_bounds__(kSweepThreads)
 half_sweep_f64(double *__restrict__ self, const double *__restrict__ other,
                const double *__restrict__ hf, int n, int W, int kact, int rows_per_block,
                double one) {
     static_assert(PTS == 2 || PTS == 4, "2 or 4 values per thread");
+    static_assert(ROWS == 1 || ROWS == 2, "1 or 2 rows per step");
     const int lane = threadIdx.x & 31;
     const int k0 = PTS * (blockIdx.x * kSweepThreads + threadIdx.x);
     const bool act = k0 < kact;  // k0 + PTS - 1 < W as W is a multiple of 32
     const int i0 = 1 + blockIdx.y * rows_per_block;
     if (i0 > n) return;  // uniform over the block
     const int i1 = min(n, i0 + rows_per_block - 1);
-    double up[PTS], mid[PTS], dn[PTS], f[PTS], r[PTS];
+    double up[PTS], mid[PTS], dn[PTS], f[PTS];
     load_row<PTS>(up, other + (size_t)(i0 - 1) * W + k0, act);
     load_row<PTS>(mid, other + (size_t)i0 * W + k0, act);
-    for (int i = i0; i <= i1; ++i) {
+    int i = i0;
+    if (ROWS == 2) {
+        double dn2[PTS], f2[PTS];
+        for (; i + 1 <= i1; i += 2) {
+            const size_t row = (size_t)i * W;
+            load_row<PTS>(dn, other + row + W + k0, act);
+            load_row<PTS>(dn2, other + row + 2 * (size_t)W + k0, act);
+            load_row<PTS>(f, hf + row + k0, act);
+            load_row<PTS>(f2, hf + row + W + k0, act);
+            update_row<COLOUR, M, PLAIN, PTS>(self, other, up, mid, dn, f, i, k0, n, W, kact, act, lane, one);
+            update_row<COLOUR, M, PLAIN, PTS>(self, other, mid, dn, dn2, f2, i + 1, k0, n, W, kact, act, lane, one);
+#pragma unroll
+            for (int q = 0; q < PTS; ++q) {
+                up[q] = dn[q];
+                mid[q] = dn2[q];
+            }
+        }
+    }
+    for (; i <= i1; ++i) {
         const size_t row = (size_t)i * W;
         load_row<PTS>(dn, other + row + W + k0, act);
         load_row<PTS>(f, hf + row + k0, act);
-        const int p = (i + COLOUR) & 1;  // column offset of this colour in row i
-        if (p == 0) {
-            // value q sits at natural column 2(k0+q): west = other[k0+q-1], east = other[k0+q]
-            double prev = __shfl_up_sync(0xffffffffu, mid[PTS - 1], 1);
-            if (lane == 0) prev = (act && k0 > 0) ? __ldg(other + row + k0 - 1) : 0.0;
-#pragma unroll
-            for (int q = 0; q < PTS; ++q)
-                r[q] = update_f64<PLAIN>((M >> (4 * (q & 1))) & 15, f[q], up[q], dn[q],
-                                         q ? mid[q - 1] : prev, mid[q], one);
-        } else {
-            // value q sits at 2(k0+q)+1: west = other[k0+q], east = other[k0+q+1]
-            double next = __shfl_down_sync(0xffffffffu, mid[0], 1);
-            if (lane == 31) next = (k0 + PTS < kact) ? __ldg(other + row + k0 + PTS) : 0.0;
-#pragma unroll
-            for (int q = 0; q < PTS; ++q)
-                r[q] = update_f64<PLAIN>((M >> (4 * (q & 1))) & 15, f[q], up[q], dn[q], mid[q],
-                                         q + 1 < PTS ? mid[q + 1] : next, one);
-        }
-        const int j0 = 2 * k0 + p;  // natural column of value 0; value q is at j0 + 2q
-        double *sp = self + row + k0;
-        if (act && j0 >= 1 && j0 + 2 * (PTS - 1) <= n) {
-            store_row<PTS>(sp, r);
-        } else if (act) {
-#pragma unroll
-            for (int q = 0; q < PTS; ++q)
-                if (j0 + 2 * q >= 1 && j0 + 2 * q <= n) sp[q] = r[q];
-        }
+        update_row<COLOUR, M, PLAIN, PTS>(self, other, up, mid, dn, f, i, k0, n, W, kact, act, lane, one);
 #pragma unroll
         for (int q = 0; q < PTS; ++q) {
             up[q] = mid[q];
@@ -78,7 +108,7 @@ half_sweep_f64(double *__restrict__ self, const double *__restrict__ other,
     }
 }
 
-template <int M, bool PLAIN, int PTS>
+template <int M, bool PLAIN, int PTS, int ROWS>
 rbgs_status launch_colour(const rbgs_ctx *c, int colour, cudaStream_t s) {
     const Geometry &g = c->g;
     const int kact = active_width(g.n);
@@ -86,10 +116,10 @@ rbgs_status launch_colour(const rbgs_ctx *c, int colour, cudaStream_t s) {
     const int per_block = PTS * kSweepThreads;
     dim3 grid((kact + per_block - 1) / per_block, (g.n + rows - 1) / rows);
     if (colour == 0)
-        half_sweep_f64<0, M, PLAIN, PTS><<<grid, kSweepThreads, 0, s>>>(c->f64.u[0], c->f64.u[1], c->f64.hf[0],
+        half_sweep_f64<0, M, PLAIN, PTS, ROWS><<<grid, kSweepThreads, 0, s>>>(c->f64.u[0], c->f64.u[1], c->f64.hf[0],
                                                                          g.n, g.W, kact, rows, 1.0);
     else
-        half_sweep_f64<1, M, PLAIN, PTS><<<grid, kSweepThreads, 0, s>>>(c->f64.u[1], c->f64.u[0], c->f64.hf[1],
+        half_sweep_f64<1, M, PLAIN, PTS, ROWS><<<grid, kSweepThreads, 0, s>>>(c->f64.u[1], c->f64.u[0], c->f64.hf[1],
                                                                          g.n, g.W, kact, rows, 1.0);
     RBGS_LAUNCH_CHECK();
     return RBGS_OK;
@@ -97,14 +127,15 @@ rbgs_status launch_colour(const rbgs_ctx *c, int colour, cudaStream_t s) {
 
 template <int PTS>
 rbgs_status launch_pts(const rbgs_ctx *c, int colour, cudaStream_t s) {
+    if (c->sweep_rows == 2 && c->emulate == 0x00) return launch_colour<0x00, false, PTS, 2>(c, colour, s);
     switch (c->emulate) {
-    case -2: return launch_colour<0x00, true, PTS>(c, colour, s);
-    case 0x00: return launch_colour<0x00, false, PTS>(c, colour, s);
-    case 0x08: return launch_colour<0x08, false, PTS>(c, colour, s);
-    case 0x88: return launch_colour<0x88, false, PTS>(c, colour, s);
-    case 0x8C: return launch_colour<0x8C, false, PTS>(c, colour, s);
-    case 0xCC: return launch_colour<0xCC, false, PTS>(c, colour, s);
-    case 0xFF: return launch_colour<0xFF, false, PTS>(c, colour, s);
+    case -2: return launch_colour<0x00, true, PTS, 1>(c, colour, s);
+    case 0x00: return launch_colour<0x00, false, PTS, 1>(c, colour, s);
+    case 0x08: return launch_colour<0x08, false, PTS, 1>(c, colour, s);
+    case 0x88: return launch_colour<0x88, false, PTS, 1>(c, colour, s);
+    case 0x8C: return launch_colour<0x8C, false, PTS, 1>(c, colour, s);
+    case 0xCC: return launch_colour<0xCC, false, PTS, 1>(c, colour, s);
+    case 0xFF: return launch_colour<0xFF, false, PTS, 1>(c, colour, s);
     default:
         set_error("unsupported FP64 emulation split 0x%x", c->emulate);
         return RBGS_EINVAL;

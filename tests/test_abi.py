@@ -52,7 +52,7 @@ def test_default_opts(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # rbgs_opts: 3 ints, a long, 5 ints -> 48 bytes on LP64; problem/result as declared
+    # rbgs_opts: 3 ints, a long, 6 ints -> 48 bytes on LP64; problem/result as declared
     assert ctypes.sizeof(rb.Opts) == 48
     assert ctypes.sizeof(rb.Problem) == 32
     assert ctypes.sizeof(rb.Result) == 32
