@@ -16,7 +16,8 @@
  * average pooling down, nearest-neighbour upsampling up, skip connections by channel
  * concatenation, widths 32/64/128/256, a final 1x1 convolution to one channel.  Input
  * channels: f, boundary mask (1 on the Dirichlet ring), boundary values g (0 off the
- * ring), zero-padded to 16 channels internally.  H and W must be multiples of 8.
+ * ring), and a smooth interpolation of g into the interior; zero-padded to 16 channels
+ * internally.  H and W must be multiples of 8.
  */
 #ifndef RBGS_UNET_H
 #define RBGS_UNET_H
@@ -70,7 +71,8 @@ rbgs_status rbgs_unet_get_params(rbgs_unet_t net, float *params);
 rbgs_status rbgs_unet_set_params(rbgs_unet_t net, const float *params);
 
 /*
- * Forward pass: x is B*H*W*3 fp32 (f, mask, g), y receives B*H*W fp32 predictions.
+ * Forward pass: x is B*H*W*4 fp32 (the four input channels), y receives B*H*W fp32
+ * predictions.
  * Buffers for B x H x W are allocated on first use and reused.
  */
 rbgs_status rbgs_unet_forward(rbgs_unet_t net, const float *x, float *y, int B, int H, int W);

@@ -91,14 +91,15 @@ def relu(x):
 
 # ------------------------------------------------------------------ network
 def forward(params, x3, keep=False):
-    """x3: B x H x W x 3 (f, mask, g).  Returns the 8-channel output (channel 0 is the
-    prediction) and, with keep=True, the cached tensors for backward."""
+    """x3: B x H x W x C input channels (C <= 16; the network reads 16, zero-padded).
+    Returns the 8-channel output (channel 0 is the prediction) and, with keep=True, the
+    cached tensors for backward."""
     sl, _ = param_slices()
     W = [params[s].reshape(shape) for s, _, shape in sl]
     Bv = [params[bs] for _, bs, _ in sl]
     b, h, w, _ = x3.shape
     x = np.zeros((b, h, w, IN_CH))
-    x[..., :3] = x3
+    x[..., :x3.shape[-1]] = x3
     cache = {"in": x}
 
     def conv(li, inp, name):

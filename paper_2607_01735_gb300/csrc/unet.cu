@@ -37,7 +37,8 @@ struct Layer {
     long w_off, b_off;  // offsets into the parameter vector
 };
 
-constexpr int kInCh = 16;  // f, mask, g, zero padding
+constexpr int kInCh = 16;  // f, mask, g, boundary interpolation, zero padding
+constexpr int kXCh = 4;    // channels of the caller's input
 const int kSpec[15][5] = {
     // cin, cout, ks, relu, level
     {16, 32, 3, 1, 0},   {32, 32, 3, 1, 0},   {32, 64, 3, 1, 1},   {64, 64, 3, 1, 1},
@@ -49,7 +50,7 @@ const int kSpec[15][5] = {
 __global__ void pack_input_kernel(const float *__restrict__ x, __nv_bfloat16 *__restrict__ out, long P) {
     for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int c = 0; c < kInCh; ++c) out[p * kInCh + c] = __float2bfloat16_rn(c < 3 ? x[p * 3 + c] : 0.f);
+        for (int c = 0; c < kInCh; ++c) out[p * kInCh + c] = __float2bfloat16_rn(c < kXCh ? x[p * kXCh + c] : 0.f);
     }
 }
 
@@ -429,7 +430,7 @@ rbgs_status rbgs_unet_create(uint64_t seed, void *cuda_stream, rbgs_unet_t *out)
     std::vector<float> h(off, 0.f);
     uint64_t st = seed;
     for (const Layer &L : net->layers) {
-        const int real_in = L.cin == kInCh ? 3 : L.cin;
+        const int real_in = L.cin == kInCh ? kXCh : L.cin;
         const float a = std::sqrt(6.0f / (float)(L.ks * L.ks * real_in));
         const long nw = (long)L.cout * L.ks * L.ks * L.cin;
         for (long q = 0; q < nw; ++q) {

@@ -8,7 +8,8 @@ Gauss-Seidel finishes to the same tolerance):
      targets (the converged grids) stay on the GPU.
   2. `train`: minibatch Adam steps, each one rbgs_unet_train_step (forward, backward and
      update in the library's kernels).
-  3. `initial_guess`: the network's prediction with the Dirichlet ring restored; for a
+  3. `initial_guess`: a transfinite interpolation of the boundary data plus the
+     network's predicted correction, with the Dirichlet ring restored; for a
      grid finer than the training grid, `initial_guess_coarse` predicts on the training
      resolution (f block-averaged, ring sampled) and interpolates bilinearly.
 The solver then runs from that u0 to the requested tolerance, exactly as from u0 = 0.
@@ -20,7 +21,7 @@ import torch
 import torch.nn.functional as F
 
 from . import default_opts, rbgs_solve_batched, RBGS_FP64, RBGS_FP32_REFINE
-from .unet import UNet, network_input
+from .unet import UNet, boundary_blend, network_input
 
 
 def grid_size(n: int) -> int:
@@ -50,8 +51,9 @@ def make_dataset(n: int, streams, tol: float = 1e-12, device="cuda", batch: int 
         res = rbgs_solve_batched(probs, tol, outs, opts)
         for (nn, _, fd, ud), sol in zip(probs, outs):
             xs.append(network_input(fd, ud, size))
+            # the network learns the correction to the boundary interpolation
             t = torch.zeros((size, size), dtype=torch.float32, device=device)
-            t[:n + 2, :n + 2] = sol.to(torch.float32)
+            t[:n + 2, :n + 2] = (sol - boundary_blend(ud)).to(torch.float32)
             ys.append(t)
     x = torch.stack(xs)
     y = torch.stack(ys)
@@ -76,13 +78,15 @@ def train(net: UNet, x, y, mask, steps: int, batch: int = 16, lr: float = 1e-3, 
 
 
 def initial_guess(net: UNet, f: torch.Tensor, u_ring: torch.Tensor) -> torch.Tensor:
-    """u0 on the (n+2)^2 grid: the network's interior prediction, the given Dirichlet ring."""
+    """u0 on the (n+2)^2 grid: boundary interpolation plus the network's correction in the
+    interior, the given Dirichlet ring."""
     n = f.shape[0]
     size = grid_size(n)
     x = network_input(f, u_ring, size).unsqueeze(0)
     pred = net.forward(x)[0]
     u0 = u_ring.clone().to(torch.float64)
-    u0[1:n + 1, 1:n + 1] = pred[1:n + 1, 1:n + 1].to(torch.float64)
+    base = boundary_blend(u_ring)
+    u0[1:n + 1, 1:n + 1] = base[1:n + 1, 1:n + 1] + pred[1:n + 1, 1:n + 1].to(torch.float64)
     return u0
 
 

@@ -3,8 +3,9 @@
 Argument marshalling only: the convolutions, pooling, upsampling, loss, backward pass
 and Adam update all run in the library's CUDA kernels.  Tensors are torch CUDA
 tensors; bf16 operands are passed as torch.bfloat16 tensors (their uint16 bit
-patterns).  `network_input` assembles the three input channels (f, boundary mask,
-boundary values) of one Poisson problem on an H x W grid padded to a multiple of 8.
+patterns).  `network_input` assembles the four input channels (f, boundary mask,
+boundary values, boundary interpolation) of one Poisson problem on an H x W grid padded
+to a multiple of 8.
 """
 from __future__ import annotations
 
@@ -12,7 +13,7 @@ import ctypes
 
 import torch
 
-from . import RbgsError, _check, load_library
+from . import _check, load_library
 
 _bound = False
 
@@ -73,18 +74,35 @@ def rbgs_conv_backward(x, w, g, dx, dw, db, accumulate=False):
                                      Cout, k, int(accumulate), _stream(x)))
 
 
+def boundary_blend(u_ring):
+    """Transfinite (Coons) interpolation of the ring values of an (N+2)^2 grid into its
+    interior: the bilinearly blended sum of the four edge interpolants minus the corner
+    bilinear term.  It reproduces boundary data that is linear in x and y exactly."""
+    g = u_ring.shape[0]
+    t = torch.linspace(0.0, 1.0, g, dtype=torch.float64, device=u_ring.device)
+    x, y = t[:, None], t[None, :]
+    u = u_ring.to(torch.float64)
+    north, south = u[0:1, :], u[g - 1:g, :]
+    west, east = u[:, 0:1], u[:, g - 1:g]
+    c00, c01, c10, c11 = u[0, 0], u[0, g - 1], u[g - 1, 0], u[g - 1, g - 1]
+    return ((1 - x) * north + x * south + (1 - y) * west + y * east
+            - ((1 - x) * (1 - y) * c00 + (1 - x) * y * c01 + x * (1 - y) * c10 + x * y * c11))
+
+
 def network_input(f, u_ring, size=None):
-    """3-channel input of one problem: f on the interior, mask 1 on the Dirichlet ring,
-    ring values; the (N+2)^2 grid zero-padded to `size` (default: multiple of 8)."""
+    """4-channel input of one problem: f on the interior, mask 1 on the Dirichlet ring,
+    ring values, and boundary_blend of the ring; the (N+2)^2 grid zero-padded to `size`
+    (default: multiple of 8)."""
     n = f.shape[0]
     g = n + 2
     size = size or (g + 7) // 8 * 8
-    x = torch.zeros((size, size, 3), dtype=torch.float32, device=f.device)
+    x = torch.zeros((size, size, 4), dtype=torch.float32, device=f.device)
     x[1:n + 1, 1:n + 1, 0] = f.to(torch.float32)
     ring = torch.ones((g, g), dtype=torch.bool, device=f.device)
     ring[1:n + 1, 1:n + 1] = False
     x[:g, :g, 1] = ring.to(torch.float32)
     x[:g, :g, 2] = torch.where(ring, u_ring.to(torch.float32), torch.zeros_like(u_ring, dtype=torch.float32))
+    x[:g, :g, 3] = boundary_blend(u_ring).to(torch.float32)
     return x
 
 
@@ -109,7 +127,7 @@ class UNet:
         _check(_lib().rbgs_unet_set_params(self.handle, _p(params)))
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
-        """x: B,H,W,3 fp32 -> B,H,W fp32."""
+        """x: B,H,W,4 fp32 -> B,H,W fp32."""
         B, H, W, _ = x.shape
         x = x.contiguous()
         y = torch.empty((B, H, W), dtype=torch.float32, device=x.device)

@@ -68,7 +68,7 @@ def test_network_gradient_matches_oracle():
     params = net.get_params().cpu().double().numpy()
     rng = np.random.default_rng(5)
     B, H, W = 2, 16, 16
-    x3 = rng.normal(size=(B, H, W, 3))
+    x3 = rng.normal(size=(B, H, W, 4))
     target = rng.normal(size=(B, H, W)) * 0.1
     mask = (rng.uniform(size=(B, H, W)) > 0.2).astype(np.float64)
     # the GPU's forward consumes bf16 weights and inputs: give the oracle the same values
@@ -86,7 +86,7 @@ def test_network_gradient_matches_oracle():
     # padded input channels carry no gradient
     sl, _ = U.param_slices()
     w0 = g[sl[0][0]].reshape(32, 3, 3, 16)
-    assert np.all(w0[..., 3:] == 0)
+    assert np.all(w0[..., 4:] == 0)
 
 
 def test_training_reduces_loss_and_forward_matches_oracle():
@@ -94,7 +94,7 @@ def test_training_reduces_loss_and_forward_matches_oracle():
     net = UNet(seed=1)
     rng = np.random.default_rng(9)
     B, H, W = 4, 16, 16
-    x = torch.from_numpy(rng.normal(size=(B, H, W, 3))).float().cuda()
+    x = torch.from_numpy(rng.normal(size=(B, H, W, 4))).float().cuda()
     t = torch.from_numpy(np.sin(rng.normal(size=(B, H, W)))).float().cuda() * 0.2
     m = torch.ones((B, H, W), device="cuda")
     losses = [net.train_step(x, t, m, lr=3e-3) for _ in range(150)]
