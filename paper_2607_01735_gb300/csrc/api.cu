@@ -338,14 +338,28 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     c->stream = (cudaStream_t)cuda_stream;
     c->kernel = o.kernel == RBGS_KERNEL_AUTO ? RBGS_KERNEL_COLOUR : o.kernel;
     c->emulate = o.fp64_emulate == -1 ? 0x00 : o.fp64_emulate;
-    c->tile_rows = o.tile_rows ? o.tile_rows : 32;
-    if (c->tile_rows < (n + 65534) / 65535) c->tile_rows = (n + 65534) / 65535;  // grid.y limit
     c->pts = o.sweep_values ? o.sweep_values : 2;
+    if (o.tile_rows) {
+        c->tile_rows = o.tile_rows;
+    } else {
+        // strips of up to 32 rows, fewer when that leaves fewer than ~4 blocks per SM
+        int sms = 0;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 152;
+        }
+        const long gx = (active_width(n) + c->pts * kSweepThreads - 1) / (c->pts * kSweepThreads);
+        long r = (long)n * gx / (4L * sms);
+        c->tile_rows = (int)(r < 1 ? 1 : (r > 32 ? 32 : r));
+    }
+    if (c->tile_rows < (n + 65534) / 65535) c->tile_rows = (n + 65534) / 65535;  // grid.y limit
     c->sweep_rows = o.sweep_rows ? o.sweep_rows : 1;
     // FP64 sweeps: temporal depth (used when kernel == TEMPORAL)
     c->tblock_k = (o.precision == RBGS_FP64 && o.tblock_k) ? o.tblock_k : 2;
-    // FP32 inner sweeps of the refinement: temporal tiles for large grids unless told otherwise
-    c->kernel32 = o.kernel == RBGS_KERNEL_AUTO ? (n >= 512 ? RBGS_KERNEL_TEMPORAL : RBGS_KERNEL_COLOUR) : o.kernel;
+    // FP32 inner sweeps of the refinement: one launch per colour unless told otherwise (the
+    // temporally blocked tiles measured slower on GB300)
+    c->kernel32 = o.kernel == RBGS_KERNEL_AUTO ? RBGS_KERNEL_COLOUR : o.kernel;
     c->tblock_k32 = (o.precision == RBGS_FP32_REFINE && o.tblock_k) ? o.tblock_k : 4;
     c->inner_sweeps = o.inner_sweeps ? o.inner_sweeps : 100;
     c->f64.n = n;

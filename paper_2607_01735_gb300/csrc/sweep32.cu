@@ -76,8 +76,11 @@ rbgs_status launch_sweeps_f32(const ColourField<float> &fld, long nsweeps, cudaS
     const int n = fld.n;
     // active values per row, rounded up to whole 4-value vectors
     const int kact = (((n + 3) / 2) + 3) & ~3;
-    const int rows = 32;
-    dim3 grid((kact + kPts32 * kSweepThreads - 1) / (kPts32 * kSweepThreads), (n + rows - 1) / rows);
+    // strips of up to 32 rows, fewer when that leaves fewer than ~600 blocks
+    const int gx = (kact + kPts32 * kSweepThreads - 1) / (kPts32 * kSweepThreads);
+    long r = (long)n * gx / 600;
+    const int rows = (int)(r < 1 ? 1 : (r > 32 ? 32 : r));
+    dim3 grid(gx, (n + rows - 1) / rows);
     for (long it = 0; it < nsweeps; ++it) {
         half_sweep_f32<0><<<grid, kSweepThreads, 0, s>>>(fld.u[0], fld.u[1], fld.hf[0], n, fld.W, kact, rows);
         RBGS_LAUNCH_CHECK();
