@@ -484,7 +484,7 @@ def main():
         inner = args.inner or 100
         outer = -(-sweeps // inner)
         k32 = args.tblock_k or 4
-        per_outer = 4 + 1 + 3 + (inner // k32 + 2 * (inner % k32) if (args.kernel == 2 or (args.kernel == 0 and n >= 512)) else 2 * inner)
+        per_outer = 4 + 1 + 3 + (inner // k32 + 2 * (inner % k32) if args.kernel == 2 else 2 * inner)
         launches_per_step = 4 + 4 + outer * per_outer + 3 + 1
     elif args.kernel == 2:
         k = args.tblock_k or 2
@@ -520,7 +520,7 @@ def main():
     temporal = args.kernel == 2
     if refine:
         # dominant kernel: the FP32 inner half-sweep (12 algorithmic bytes per update)
-        kname = "temporal_tile<float>" if temporal or (args.kernel == 0 and n >= 512) else "half_sweep_f32"
+        kname = "temporal_tile<float>" if temporal else "half_sweep_f32"
         per_launch_lups = n * n / 2.0
         launch_s = sweep_s / (2 * sweeps * args.steps)  # per half-sweep equivalent
         alg_bytes = 12 * per_launch_lups
