@@ -52,7 +52,7 @@ cudaError_t encode_tensor_map_2d(CUtensorMap *map, const void *base, int elem_by
 
 namespace {
 
-constexpr int kTThreads = 1024;
+constexpr int kTThreads = 512;
 constexpr uint32_t kWaitPolls = 1u << 22;  // bounded mbarrier wait
 
 template <typename T, int K, int TR, int TK>
@@ -93,8 +93,49 @@ struct Update<float> {
     }
 };
 
+// One row of a half-step: the row's colour offset P (0 or 1) is a compile-time constant,
+// so the neighbour that comes from the adjacent lane, and its direction, are fixed.
+template <typename T, int EK, int P>
+__device__ __forceinline__ void tile_row(T *__restrict__ self, const T *__restrict__ oth, const T *__restrict__ fh,
+                                         int ii, int kk, int lane, T &up, T &mid, bool store, double one) {
+    const T dn = oth[(ii + 1) * EK + kk];
+    const T fv = fh[ii * EK + kk];
+    T vw, ve;
+    if (P == 0) {  // west neighbour is column kk-1 (the previous lane)
+        T prev = __shfl_up_sync(0xffffffffu, mid, 1);
+        if (lane == 0) prev = kk > 0 ? oth[ii * EK + kk - 1] : T(0);
+        vw = prev;
+        ve = mid;
+    } else {       // east neighbour is column kk+1 (the next lane)
+        T next = __shfl_down_sync(0xffffffffu, mid, 1);
+        if (lane == 31) next = kk + 1 < EK ? oth[ii * EK + kk + 1] : T(0);
+        vw = mid;
+        ve = next;
+    }
+    const T r = Update<T>::go(fv, up, dn, vw, ve, one);
+    if (store) self[ii * EK + kk] = r;
+    up = mid;
+    mid = dn;
+}
+
+// Rows [r0, r1) of one half-step, in pairs (the colour offset alternates row by row).
+template <typename T, int EK, int P0>
+__device__ __forceinline__ void tile_rows(T *__restrict__ self, const T *__restrict__ oth, const T *__restrict__ fh,
+                                          int r0, int r1, int row_lo, int row_hi, int kk, int lane, bool col0,
+                                          bool col1, double one) {
+    T up = oth[(r0 - 1) * EK + kk];
+    T mid = oth[r0 * EK + kk];
+    for (int ii = r0; ii < r1; ii += 2) {
+        tile_row<T, EK, P0>(self, oth, fh, ii, kk, lane, up, mid,
+                            (P0 == 0 ? col0 : col1) && ii >= row_lo && ii < row_hi, one);
+        if (ii + 1 < r1)
+            tile_row<T, EK, 1 - P0>(self, oth, fh, ii + 1, kk, lane, up, mid,
+                                    (P0 == 0 ? col1 : col0) && ii + 1 >= row_lo && ii + 1 < row_hi, one);
+    }
+}
+
 template <typename T, int K, int TR, int TK>
-__global__ void __launch_bounds__(kTThreads)
+__global__ void __launch_bounds__(kTThreads, 2)
 temporal_tile(const __grid_constant__ CUtensorMap mu0, const __grid_constant__ CUtensorMap mu1,
               const __grid_constant__ CUtensorMap mf0, const __grid_constant__ CUtensorMap mf1,
               T *__restrict__ out0, T *__restrict__ out1, int n, int W, double one, int *status) {
@@ -140,6 +181,8 @@ temporal_tile(const __grid_constant__ CUtensorMap mu0, const __grid_constant__ C
     constexpr int BANDS = kTThreads / C::EK;
     const int kk = threadIdx.x % C::EK, band = threadIdx.x / C::EK;
     const int lane = threadIdx.x & 31;
+    // interior rows of the grid, as smem row indices: R0 + ii in [1, n]
+    const int row_lo = 1 - R0, row_hi = n + 1 - R0;
     for (int s = 0; s < 2 * K; ++s) {
         const int c = s & 1;
         T *const self = c ? su1 : su0;
@@ -149,40 +192,34 @@ temporal_tile(const __grid_constant__ CUtensorMap mu0, const __grid_constant__ C
         const int per = (rhi - rlo + BANDS - 1) / BANDS;
         const int r0 = rlo + band * per;
         const int r1 = r0 + per < rhi ? r0 + per : rhi;
+        // column kk holds natural column jj = 2 kk + p of the region (p = the row's offset);
+        // it is updated at this step if it lies at distance > s from the region's edge and
+        // inside the grid
+        bool colok[2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int jj = 2 * kk + p, j = 2 * E0 + jj;
+            colok[p] = jj >= s + 1 && (2 * C::EK - 1 - jj) >= s + 1 && j >= 1 && j <= n;
+        }
         if (r0 < r1) {
-            T up = oth[(r0 - 1) * C::EK + kk];
-            T mid = oth[r0 * C::EK + kk];
-            for (int ii = r0; ii < r1; ++ii) {
-                const T dn = oth[(ii + 1) * C::EK + kk];
-                const T fv = fh[ii * C::EK + kk];
-                const int i = R0 + ii;
-                const int p = (i + c) & 1;  // column offset of colour c in row i
-                T prev = __shfl_up_sync(0xffffffffu, mid, 1);
-                T next = __shfl_down_sync(0xffffffffu, mid, 1);
-                if (lane == 0) prev = kk > 0 ? oth[ii * C::EK + kk - 1] : T(0);
-                if (lane == 31) next = kk + 1 < C::EK ? oth[ii * C::EK + kk + 1] : T(0);
-                const T vw = p ? mid : prev, ve = p ? next : mid;
-                const T r = Update<T>::go(fv, up, dn, vw, ve, one);
-                const int jj = 2 * kk + p;  // natural column relative to the region's first column
-                const int j = 2 * E0 + jj;
-                const bool valid = jj >= s + 1 && (2 * C::EK - 1 - jj) >= s + 1 && i >= 1 && i <= n &&
-                                   j >= 1 && j <= n;
-                if (valid) self[ii * C::EK + kk] = r;
-                up = mid;
-                mid = dn;
-            }
+            if (((R0 + r0 + c) & 1) == 0)
+                tile_rows<T, C::EK, 0>(self, oth, fh, r0, r1, row_lo, row_hi, kk, lane, colok[0], colok[1], one);
+            else
+                tile_rows<T, C::EK, 1>(self, oth, fh, r0, r1, row_lo, row_hi, kk, lane, colok[0], colok[1], one);
         }
         __syncthreads();
     }
 
     // inner tile of both colours -> partner buffers (rows 0..n+1, values 0..W-1)
-    for (int idx = threadIdx.x; idx < TR * TK; idx += kTThreads) {
-        const int ii = idx / TK, kk = idx % TK;
-        const int i = r0 + ii, k = k0 + kk;
-        if (i <= n + 1 && k < W) {
-            const int sidx = (ii + C::H) * C::EK + kk + C::HK;
-            out0[(size_t)i * W + k] = su0[sidx];
-            out1[(size_t)i * W + k] = su1[sidx];
+    if (kk >= C::HK && kk < C::HK + TK) {
+        const int k = k0 + kk - C::HK;
+        for (int rr = band; rr < TR; rr += BANDS) {
+            const int i = r0 + rr;
+            if (i <= n + 1 && k < W) {
+                const int sidx = (rr + C::H) * C::EK + kk;
+                out0[(size_t)i * W + k] = su0[sidx];
+                out1[(size_t)i * W + k] = su1[sidx];
+            }
         }
     }
 }
