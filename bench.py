@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--tile-rows", type=int, default=0)
     p.add_argument("--values", type=int, default=0, help="values per thread in a half-sweep (0 auto, 2, 4)")
     p.add_argument("--rows", type=int, default=0, help="rows per loop step in a half-sweep (0 auto, 1, 2)")
+    p.add_argument("--int-rows", type=int, default=0, help="hybrid FP64: integer-pipe rows per strip pair")
     p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one launch per colour, 2 temporal")
     p.add_argument("--tblock-k", type=int, default=0, help="sweeps per temporal pass (0 auto)")
     p.add_argument("--precision", choices=["fp64", "refine"], default="fp64",
@@ -448,7 +449,8 @@ def main():
     out = torch.empty_like(u0)
     refine = args.precision == "refine"
     opts = rb.default_opts(fp64_emulate=args.emulate, tile_rows=args.tile_rows, kernel=args.kernel,
-                           sweep_values=args.values, sweep_rows=args.rows, tblock_k=args.tblock_k,
+                           sweep_values=args.values, sweep_rows=args.rows, int_rows=args.int_rows,
+                           tblock_k=args.tblock_k,
                            precision=rb.RBGS_FP32_REFINE if refine else rb.RBGS_FP64,
                            inner_sweeps=args.inner, max_sweeps=sweeps)
     lib = rb.load_library()
@@ -589,6 +591,7 @@ def main():
                        "tblock_k": args.tblock_k or "auto", "precision": args.precision,
                        "fp64_emulate": args.emulate, "tile_rows": args.tile_rows or "auto",
                        "sweep_values": args.values or "auto", "sweep_rows": args.rows or "auto",
+                       "int_rows": args.int_rows,
                        "l2": "inputs larger than L2 (4 colour arrays of 1.08 GB each)",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs_algorithmic": BYTES_PER_LUP * lups / elapsed / 1e9,

@@ -70,6 +70,9 @@ typedef struct {
     int inner_sweeps;  /* FP32 sweeps per defect correction for RBGS_FP32_REFINE (0: auto) */
     int sweep_values;  /* values each thread updates per row in a half-sweep: 2 or 4 (0: auto) */
     int sweep_rows;    /* rows each thread updates per loop step in a half-sweep: 1 or 2 (0: auto) */
+    int int_rows;      /* FP64 hybrid half-sweep: between strips of tile_rows rows whose adds run on
+                          the FP64 pipe, strips of int_rows rows whose adds run as exact integer
+                          IEEE additions (same results; 0: off, -1: automatic)                  */
 } rbgs_opts;
 
 /* Fills *opts with the defaults (all automatic). */

@@ -46,7 +46,7 @@ class Opts(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("max_sweeps", ctypes.c_long),
                 ("tblock_k", ctypes.c_int), ("tile_rows", ctypes.c_int),
                 ("fp64_emulate", ctypes.c_int), ("inner_sweeps", ctypes.c_int),
-                ("sweep_values", ctypes.c_int), ("sweep_rows", ctypes.c_int)]
+                ("sweep_values", ctypes.c_int), ("sweep_rows", ctypes.c_int), ("int_rows", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):

@@ -317,6 +317,9 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     if (o.sweep_values != 0 && o.sweep_values != 2 && o.sweep_values != 4) {
         set_error("sweep_values must be 0, 2 or 4"); return RBGS_EINVAL;
     }
+    if (o.int_rows < -1) {
+        set_error("int_rows must be >= -1"); return RBGS_EINVAL;
+    }
     if (o.sweep_rows != 0 && o.sweep_rows != 1 && o.sweep_rows != 2) {
         set_error("sweep_rows must be 0, 1 or 2"); return RBGS_EINVAL;
     }
@@ -355,6 +358,7 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     }
     if (c->tile_rows < (n + 65534) / 65535) c->tile_rows = (n + 65534) / 65535;  // grid.y limit
     c->sweep_rows = o.sweep_rows ? o.sweep_rows : 1;
+    c->int_rows = o.int_rows > 0 ? o.int_rows : 0;
     // FP64 sweeps: temporal depth (used when kernel == TEMPORAL)
     c->tblock_k = (o.precision == RBGS_FP64 && o.tblock_k) ? o.tblock_k : 2;
     // FP32 inner sweeps of the refinement: one launch per colour unless told otherwise (the

@@ -98,6 +98,7 @@ struct rbgs_ctx {
     int tile_rows;              // resolved rows per block
     int pts;                    // values per thread in the half-sweep (2 or 4)
     int sweep_rows;             // rows per loop step in the half-sweep (1 or 2)
+    int int_rows;               // hybrid FP64 half-sweep: integer-pipe rows per strip pair (0: off)
     int tblock_k;               // resolved temporal depth (FP64)
     int tblock_k32;             // resolved temporal depth (FP32 inner sweeps)
     int inner_sweeps;           // resolved FP32 sweeps per correction

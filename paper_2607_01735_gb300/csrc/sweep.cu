@@ -61,19 +61,16 @@ __device__ __forceinline__ void update_row(double *__restrict__ self, const doub
     }
 }
 
+// Rows i0..i1 of one strip (the body of a half-sweep block).
 template <int COLOUR, int M, bool PLAIN, int PTS, int ROWS>
-__global__ void __launch_bounds__(kSweepThreads)
-half_sweep_f64(double *__restrict__ self, const double *__restrict__ other,
-               const double *__restrict__ hf, int n, int W, int kact, int rows_per_block,
-               double one) {
+__device__ __forceinline__ void march_strip(double *__restrict__ self, const double *__restrict__ other,
+                                            const double *__restrict__ hf, int n, int W, int kact, int i0, int i1,
+                                            double one) {
     static_assert(PTS == 2 || PTS == 4, "2 or 4 values per thread");
     static_assert(ROWS == 1 || ROWS == 2, "1 or 2 rows per step");
     const int lane = threadIdx.x & 31;
     const int k0 = PTS * (blockIdx.x * kSweepThreads + threadIdx.x);
     const bool act = k0 < kact;  // k0 + PTS - 1 < W as W is a multiple of 32
-    const int i0 = 1 + blockIdx.y * rows_per_block;
-    if (i0 > n) return;  // uniform over the block
-    const int i1 = min(n, i0 + rows_per_block - 1);
     double up[PTS], mid[PTS], dn[PTS], f[PTS];
     load_row<PTS>(up, other + (size_t)(i0 - 1) * W + k0, act);
     load_row<PTS>(mid, other + (size_t)i0 * W + k0, act);
@@ -108,6 +105,38 @@ half_sweep_f64(double *__restrict__ self, const double *__restrict__ other,
     }
 }
 
+template <int COLOUR, int M, bool PLAIN, int PTS, int ROWS>
+__global__ void __launch_bounds__(kSweepThreads)
+half_sweep_f64(double *__restrict__ self, const double *__restrict__ other,
+               const double *__restrict__ hf, int n, int W, int kact, int rows_per_block,
+               double one) {
+    const int i0 = 1 + blockIdx.y * rows_per_block;
+    if (i0 > n) return;  // uniform over the block
+    const int i1 = min(n, i0 + rows_per_block - 1);
+    march_strip<COLOUR, M, PLAIN, PTS, ROWS>(self, other, hf, n, W, kact, i0, i1, one);
+}
+
+// Hybrid half-sweep: the rows are cut into repeating pairs of strips, rows_fp rows whose
+// adds run on the FP64 pipe and rows_int rows whose adds run on the integer pipe (exact
+// IEEE addition, fp64.cuh).  Block y handles strip y; both kinds of blocks are resident on
+// every SM at once, so the two pipes work in parallel while each warp stays on one pipe.
+// The result is bit-identical to every other variant.
+template <int COLOUR, int PTS>
+__global__ void __launch_bounds__(kSweepThreads)
+half_sweep_f64_hybrid(double *__restrict__ self, const double *__restrict__ other,
+                      const double *__restrict__ hf, int n, int W, int kact, int rows_fp, int rows_int,
+                      double one) {
+    const int period = rows_fp + rows_int;
+    const int pair = blockIdx.y >> 1, kind = blockIdx.y & 1;
+    const int i0 = 1 + pair * period + (kind ? rows_fp : 0);
+    if (i0 > n) return;  // uniform over the block
+    const int i1 = min(n, i0 + (kind ? rows_int : rows_fp) - 1);
+    if (kind == 0)
+        march_strip<COLOUR, 0x00, false, PTS, 1>(self, other, hf, n, W, kact, i0, i1, one);
+    else
+        march_strip<COLOUR, 0xFF, false, PTS, 1>(self, other, hf, n, W, kact, i0, i1, one);
+}
+
 template <int M, bool PLAIN, int PTS, int ROWS>
 rbgs_status launch_colour(const rbgs_ctx *c, int colour, cudaStream_t s) {
     const Geometry &g = c->g;
@@ -126,7 +155,26 @@ rbgs_status launch_colour(const rbgs_ctx *c, int colour, cudaStream_t s) {
 }
 
 template <int PTS>
+rbgs_status launch_hybrid(const rbgs_ctx *c, int colour, cudaStream_t s) {
+    const Geometry &g = c->g;
+    const int kact = active_width(g.n);
+    const int rf = c->tile_rows, ri = c->int_rows;
+    const int per_block = PTS * kSweepThreads;
+    const int pairs = (g.n + rf + ri - 1) / (rf + ri);
+    dim3 grid((kact + per_block - 1) / per_block, 2 * pairs);
+    if (colour == 0)
+        half_sweep_f64_hybrid<0, PTS><<<grid, kSweepThreads, 0, s>>>(c->f64.u[0], c->f64.u[1], c->f64.hf[0], g.n, g.W,
+                                                                     kact, rf, ri, 1.0);
+    else
+        half_sweep_f64_hybrid<1, PTS><<<grid, kSweepThreads, 0, s>>>(c->f64.u[1], c->f64.u[0], c->f64.hf[1], g.n, g.W,
+                                                                     kact, rf, ri, 1.0);
+    RBGS_LAUNCH_CHECK();
+    return RBGS_OK;
+}
+
+template <int PTS>
 rbgs_status launch_pts(const rbgs_ctx *c, int colour, cudaStream_t s) {
+    if (c->int_rows > 0) return launch_hybrid<PTS>(c, colour, s);
     if (c->sweep_rows == 2 && c->emulate == 0x00) return launch_colour<0x00, false, PTS, 2>(c, colour, s);
     switch (c->emulate) {
     case -2: return launch_colour<0x00, true, PTS, 1>(c, colour, s);

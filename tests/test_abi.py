@@ -52,8 +52,8 @@ def test_default_opts(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # rbgs_opts: 3 ints, a long, 6 ints -> 48 bytes on LP64; problem/result as declared
-    assert ctypes.sizeof(rb.Opts) == 48
+    # rbgs_opts: 3 ints (+4 padding), a long, 7 ints (+4 padding) -> 56 bytes on LP64
+    assert ctypes.sizeof(rb.Opts) == 56
     assert ctypes.sizeof(rb.Problem) == 32
     assert ctypes.sizeof(rb.Result) == 32
 

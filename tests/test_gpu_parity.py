@@ -65,13 +65,13 @@ def _assert_bits(got, ref):
 SIZES = [1, 2, 3, 4, 5, 6, 7, 8, 9, 16, 31, 32, 33, 63, 64, 127, 255, 256, 257, 300, 509, 1000, 1030]
 
 
-@pytest.mark.parametrize("values,step_rows", [(2, 1), (4, 1), (2, 2)])
+@pytest.mark.parametrize("values,step_rows,int_rows", [(2, 1, 0), (4, 1, 0), (2, 2, 0), (2, 1, 8)])
 @pytest.mark.parametrize("n", SIZES)
-def test_bit_exact_against_oracle(n, values, step_rows):
+def test_bit_exact_against_oracle(n, values, step_rows, int_rows):
     f, u0 = _problem(n, 11 + n)
     h2 = synth.h_squared(n)
     sweeps = 7 if n > 300 else 13
-    got, rho = _run_gpu(n, h2, f, u0, sweeps, sweep_values=values, sweep_rows=step_rows)
+    got, rho = _run_gpu(n, h2, f, u0, sweeps, sweep_values=values, sweep_rows=step_rows, int_rows=int_rows)
     ref = u0.copy()
     oracle.sweeps(ref, f, h2, sweeps)
     _assert_bits(got, ref)
@@ -91,13 +91,15 @@ def test_every_fp64_add_split_is_bit_exact(n, emulate, values):
     _assert_bits(got, ref)
 
 
+@pytest.mark.parametrize("int_rows", [0, 3])
 @pytest.mark.parametrize("values,step_rows", [(2, 1), (4, 1), (2, 2), (4, 2)])
 @pytest.mark.parametrize("rows", [1, 2, 7, 32, 64, 200])
-def test_strip_heights(rows, values, step_rows):
+def test_strip_heights(rows, values, step_rows, int_rows):
     n = 203
     f, u0 = _problem(n, 300 + rows)
     h2 = synth.h_squared(n)
-    got, _ = _run_gpu(n, h2, f, u0, 5, tile_rows=rows, sweep_values=values, sweep_rows=step_rows)
+    got, _ = _run_gpu(n, h2, f, u0, 5, tile_rows=rows, sweep_values=values, sweep_rows=step_rows,
+                      int_rows=int_rows)
     ref = u0.copy()
     oracle.sweeps(ref, f, h2, 5)
     _assert_bits(got, ref)
