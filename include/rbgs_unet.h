@@ -56,6 +56,26 @@ rbgs_status rbgs_conv_backward(const uint16_t *X, const uint16_t *Wt, const uint
                                float *dW, float *db, uint16_t *Wt_t, int B, int H, int W, int Cin,
                                int Cout, int ksize, int accumulate, void *cuda_stream);
 
+/*
+ * Engine of the convolution kernels (process-wide; applies to the network too):
+ *   RBGS_CONV_TCGEN05  (default) 5th-generation tensor cores: tcgen05.mma from shared-memory
+ *                      descriptors, FP32 accumulators in tensor memory, 128-row tiles;
+ *   RBGS_CONV_MMA_SYNC warp-level mma.sync tiles with register accumulators.
+ * Both compute the same sums in FP32 (the order of accumulation differs).  Returns
+ * RBGS_EINVAL for another value.  rbgs_conv_get_engine returns the current engine.
+ */
+#define RBGS_CONV_TCGEN05 0
+#define RBGS_CONV_MMA_SYNC 1
+rbgs_status rbgs_conv_set_engine(int engine);
+int rbgs_conv_get_engine(void);
+
+/*
+ * Synchronises `cuda_stream` and reports whether a tcgen05 convolution launched since
+ * the last check gave up one of its bounded waits on the tensor cores (RBGS_ETIMEOUT; its
+ * output is then incomplete).  Clears the condition.  RBGS_OK otherwise.
+ */
+rbgs_status rbgs_conv_check(void *cuda_stream);
+
 /* -------------------------------------------------------------------- network --- */
 
 typedef struct rbgs_unet *rbgs_unet_t;

@@ -1,5 +1,9 @@
 // Convolution kernels of the learned initial guess: implicit GEMM on the tensor cores.
 //
+// Two engines compute the same products: the tcgen05 kernels of conv_umma.cu (TMEM
+// accumulators, the default) and the mma.sync kernels below (register accumulators),
+// kept as the reference engine that rbgs_conv_set_engine selects.
+//
 // All three products of a 3x3 (or 1x1) convolution layer are one GEMM with a gathered
 // operand (M x N += M x K times K x N, bf16 operands, FP32 accumulation) computed with
 // mma.sync m16n8k16 bf16 tiles:
@@ -230,10 +234,22 @@ __global__ void bias_grad_kernel(const uint16_t *__restrict__ G, float *__restri
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+int g_engine = RBGS_CONV_TCGEN05;
+
 }  // namespace
+
+rbgs_status umma_conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y, int B, int H,
+                              int W, int Cin, int Cout, int ks, int relu, int y_fp32, cudaStream_t s);
+rbgs_status umma_conv_backward_data(const uint16_t *Wtt, const uint16_t *G, float *dX, int B, int H, int W,
+                                    int Cin, int Cout, int ks, int accumulate, cudaStream_t s);
+rbgs_status umma_conv_backward_weight(const uint16_t *X, const uint16_t *G, float *dW, int B, int H, int W,
+                                      int Cin, int Cout, int ks, cudaStream_t s);
+rbgs_status umma_conv_check(cudaStream_t s);
 
 rbgs_status conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y, int B, int H,
                          int W, int Cin, int Cout, int ks, int relu, int y_fp32, cudaStream_t s) {
+    if (g_engine == RBGS_CONV_TCGEN05)
+        return umma_conv_forward(X, Wt, bias, Y, B, H, W, Cin, Cout, ks, relu, y_fp32, s);
     ConvArgs a{X, Wt, nullptr, bias, Y, B, H, W, Cin, Cout, ks, relu, y_fp32, 0, 0};
     const long P = (long)B * H * W;
     dim3 grid((unsigned)((P + BM - 1) / BM), (unsigned)((Cout + BN - 1) / BN), 1);
@@ -250,12 +266,20 @@ rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t 
     if (dX) {
         transpose_weights_kernel<<<256, 256, 0, s>>>(Wt, Wtt, Cout, taps, Cin);
         RBGS_LAUNCH_CHECK();
-        ConvArgs a{X, Wtt, G, nullptr, dX, B, H, W, Cin, Cout, ks, 0, 0, accumulate, 0};
-        dim3 grid((unsigned)((P + BM - 1) / BM), (unsigned)((Cin + BN - 1) / BN), 1);
-        conv_igemm_kernel<BWD_DATA><<<grid, THREADS, 0, s>>>(a);
-        RBGS_LAUNCH_CHECK();
+        if (g_engine == RBGS_CONV_TCGEN05) {
+            const rbgs_status st = umma_conv_backward_data(Wtt, G, dX, B, H, W, Cin, Cout, ks, accumulate, s);
+            if (st != RBGS_OK) return st;
+        } else {
+            ConvArgs a{X, Wtt, G, nullptr, dX, B, H, W, Cin, Cout, ks, 0, 0, accumulate, 0};
+            dim3 grid((unsigned)((P + BM - 1) / BM), (unsigned)((Cin + BN - 1) / BN), 1);
+            conv_igemm_kernel<BWD_DATA><<<grid, THREADS, 0, s>>>(a);
+            RBGS_LAUNCH_CHECK();
+        }
     }
-    if (dW) {
+    if (dW && g_engine == RBGS_CONV_TCGEN05) {
+        const rbgs_status st = umma_conv_backward_weight(X, G, dW, B, H, W, Cin, Cout, ks, s);
+        if (st != RBGS_OK) return st;
+    } else if (dW) {
         const int chunk = 4096;
         ConvArgs a{X, Wt, G, nullptr, dW, B, H, W, Cin, Cout, ks, 0, 0, 1, chunk};
         dim3 grid((unsigned)((Cout + BM - 1) / BM), (unsigned)((taps * Cin + BN - 1) / BN),
@@ -273,7 +297,7 @@ rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t 
 
 bool conv_shapes_ok(int B, int H, int W, int Cin, int Cout, int ks) {
     return B >= 1 && H >= 1 && W >= 1 && Cin >= 8 && Cout >= 8 && Cin % 8 == 0 && Cout % 8 == 0 &&
-           (ks == 1 || ks == 3) && (long)B * H * W < (1L << 40);
+           (ks == 1 || ks == 3) && H <= 32767 && W <= 32767 && (long)B * H * W < (1L << 40);
 }
 
 }  // namespace rbgs
@@ -302,4 +326,21 @@ extern "C" rbgs_status rbgs_conv_backward(const uint16_t *X, const uint16_t *Wt,
     }
     return conv_backward(X, Wt, G, dX, dW, db, Wt_t, B, H, W, Cin, Cout, ksize, accumulate,
                          (cudaStream_t)cuda_stream);
+}
+
+extern "C" rbgs_status rbgs_conv_set_engine(int engine) {
+    clear_error();
+    if (engine != RBGS_CONV_TCGEN05 && engine != RBGS_CONV_MMA_SYNC) {
+        set_error("rbgs_conv_set_engine: unknown engine %d", engine);
+        return RBGS_EINVAL;
+    }
+    g_engine = engine;
+    return RBGS_OK;
+}
+
+extern "C" int rbgs_conv_get_engine(void) { return g_engine; }
+
+extern "C" rbgs_status rbgs_conv_check(void *cuda_stream) {
+    clear_error();
+    return umma_conv_check((cudaStream_t)cuda_stream);
 }

@@ -26,6 +26,7 @@ namespace rbgs {
 
 rbgs_status conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y, int B, int H,
                          int W, int Cin, int Cout, int ks, int relu, int y_fp32, cudaStream_t s);
+rbgs_status umma_conv_check(cudaStream_t s);
 rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t *G, float *dX, float *dW,
                           float *db, uint16_t *Wtt, int B, int H, int W, int Cin, int Cout, int ks,
                           int accumulate, cudaStream_t s);
@@ -528,7 +529,7 @@ rbgs_status rbgs_unet_train_step(rbgs_unet_t net, const float *x, const float *t
     RBGS_CUDA(cudaMemcpyAsync(net->hloss, net->dloss, 4, cudaMemcpyDeviceToHost, net->stream));
     RBGS_CUDA(cudaStreamSynchronize(net->stream));
     if (loss) *loss = *net->hloss;
-    return RBGS_OK;
+    return umma_conv_check(net->stream);
 }
 
 void rbgs_unet_destroy(rbgs_unet_t net) {

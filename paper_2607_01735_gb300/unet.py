@@ -41,6 +41,12 @@ def _lib():
         lib.rbgs_unet_train_step.restype = ci
         lib.rbgs_unet_destroy.argtypes = [vp]
         lib.rbgs_unet_destroy.restype = None
+        lib.rbgs_conv_set_engine.argtypes = [ci]
+        lib.rbgs_conv_set_engine.restype = ci
+        lib.rbgs_conv_get_engine.argtypes = []
+        lib.rbgs_conv_get_engine.restype = ci
+        lib.rbgs_conv_check.argtypes = [vp]
+        lib.rbgs_conv_check.restype = ci
         _bound = True
     return lib
 
@@ -55,6 +61,27 @@ def _p(t):
 
 def _stream(t):
     return torch.cuda.current_stream(t.device).cuda_stream
+
+
+RBGS_CONV_TCGEN05 = 0
+RBGS_CONV_MMA_SYNC = 1
+
+
+def rbgs_conv_set_engine(engine: int) -> None:
+    """Selects the convolution engine process-wide: RBGS_CONV_TCGEN05 (tensor memory
+    accumulators, default) or RBGS_CONV_MMA_SYNC (warp-level tiles)."""
+    _check(_lib().rbgs_conv_set_engine(int(engine)))
+
+
+def rbgs_conv_get_engine() -> int:
+    return int(_lib().rbgs_conv_get_engine())
+
+
+def rbgs_conv_check(device=None) -> None:
+    """Synchronises the current stream; raises RbgsError(RBGS_ETIMEOUT) if a tcgen05
+    convolution gave up a bounded wait since the last check."""
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    _check(_lib().rbgs_conv_check(torch.cuda.current_stream(dev).cuda_stream))
 
 
 def rbgs_conv_forward(x, w, bias, y, relu=True):

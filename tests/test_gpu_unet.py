@@ -32,9 +32,36 @@ def _bf(a):
     return torch.from_numpy(a).to(torch.float32).to(torch.bfloat16)
 
 
-@pytest.mark.parametrize("B,H,W,Cin,Cout,k", [(2, 8, 8, 16, 32, 3), (1, 13, 11, 32, 64, 3), (2, 16, 16, 96, 32, 3),
-                                              (3, 9, 7, 32, 8, 1), (1, 33, 40, 384, 128, 3)])
-def test_conv_forward_and_backward_match_oracle(B, H, W, Cin, Cout, k):
+ENGINES = {"tcgen05": 0, "mma_sync": 1}
+
+# shapes: ragged pixel tiles (B H W not a multiple of 128), every N-tile width the
+# tcgen05 kernel picks (16 for Cout 8, 48, 192 for 384 = 2 x 192, 256), 1x1 kernels,
+# weight gradients split over several pixel chunks (4608 and 8192 pixels)
+CONV_SHAPES = [(2, 8, 8, 16, 32, 3), (1, 13, 11, 32, 64, 3), (2, 16, 16, 96, 32, 3), (3, 9, 7, 32, 8, 1),
+               (1, 33, 40, 384, 128, 3), (1, 7, 5, 8, 48, 3), (2, 48, 48, 16, 256, 3), (2, 64, 64, 32, 16, 3),
+               (1, 10, 12, 256, 256, 1)]
+
+
+@pytest.fixture(params=list(ENGINES))
+def engine(request):
+    from paper_2607_01735_gb300 import unet as un
+    prev = un.rbgs_conv_get_engine()
+    un.rbgs_conv_set_engine(ENGINES[request.param])
+    yield request.param
+    un.rbgs_conv_check()
+    un.rbgs_conv_set_engine(prev)
+
+
+def test_engine_selection_rejects_unknown_values():
+    from paper_2607_01735_gb300 import unet as un
+    assert un.rbgs_conv_get_engine() == un.RBGS_CONV_TCGEN05
+    with pytest.raises(rb.RbgsError):
+        un.rbgs_conv_set_engine(7)
+    assert un.rbgs_conv_get_engine() == un.RBGS_CONV_TCGEN05
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout,k", CONV_SHAPES)
+def test_conv_forward_and_backward_match_oracle(B, H, W, Cin, Cout, k, engine):
     from paper_2607_01735_gb300 import unet as un
     rng = np.random.default_rng(Cin + Cout + k)
     x = _bf(rng.normal(size=(B, H, W, Cin)))
@@ -60,9 +87,40 @@ def test_conv_forward_and_backward_match_oracle(B, H, W, Cin, Cout, k):
     un.rbgs_conv_forward(xd, wd, bd, yb, relu=True)
     ref = np.maximum(y_ref, 0)
     assert np.max(np.abs(yb.float().cpu().numpy() - ref)) <= 1e-2 * np.max(np.abs(ref))
+    # accumulate mode of the data gradient adds to what dX holds
+    dx2 = dx.clone()
+    un.rbgs_conv_backward(xd, wd, gd, dx2, None, None, accumulate=True)
+    un.rbgs_conv_check()
+    got = dx2.cpu().double().numpy()
+    assert np.max(np.abs(got - 2 * dx_ref)) <= 2e-4 * np.max(np.abs(dx_ref)) + 1e-6
 
 
-def test_network_gradient_matches_oracle():
+@pytest.mark.parametrize("B,H,W,Cin,Cout,k", CONV_SHAPES[:6])
+def test_conv_engines_agree(B, H, W, Cin, Cout, k):
+    """tcgen05 (TMEM accumulators) and mma.sync (register accumulators) form the same FP32
+    sums of the same bf16 products: they differ by accumulation order only."""
+    from paper_2607_01735_gb300 import unet as un
+    rng = np.random.default_rng(3 * Cin + Cout)
+    x = _bf(rng.normal(size=(B, H, W, Cin))).cuda()
+    w = _bf(rng.normal(size=(Cout, k, k, Cin)) / np.sqrt(k * k * Cin)).cuda()
+    g = _bf(rng.normal(size=(B, H, W, Cout))).cuda()
+    outs = {}
+    for name, e in ENGINES.items():
+        un.rbgs_conv_set_engine(e)
+        y = torch.empty((B, H, W, Cout), dtype=torch.float32, device="cuda")
+        un.rbgs_conv_forward(x, w, None, y, relu=False)
+        dx = torch.empty((B, H, W, Cin), dtype=torch.float32, device="cuda")
+        dw = torch.zeros((Cout, k, k, Cin), dtype=torch.float32, device="cuda")
+        un.rbgs_conv_backward(x, w, g, dx, dw, None)
+        un.rbgs_conv_check()
+        outs[name] = (y, dx, dw)
+    un.rbgs_conv_set_engine(un.RBGS_CONV_TCGEN05)
+    for a, b in zip(outs["tcgen05"], outs["mma_sync"]):
+        scale = float(b.abs().max())
+        assert float((a - b).abs().max()) <= 1e-5 * scale + 1e-6
+
+
+def test_network_gradient_matches_oracle(engine):
     from paper_2607_01735_gb300.unet import UNet
     net = UNet(seed=7)
     params = net.get_params().cpu().double().numpy()
