@@ -1,29 +1,42 @@
 // Convolution kernels of the learned initial guess on the 5th-generation tensor cores:
 // implicit GEMM with tcgen05.mma, FP32 accumulators in tensor memory (TMEM).
 //
-// The three products of a convolution layer are the GEMMs listed in conv.cu; here they
-// are tiled for tcgen05 as follows (M x N output tile, K in stages of 64):
-//   forward      M = pixels,       N = Cout, K = taps*Cin   A, B K-major
-//   data grad    M = pixels,       N = Cin,  K = taps*Cout  A, B K-major
-//   weight grad  M = taps*Cin,     N = Cout, K = pixels     A, B MN-major (split over K)
-// (the weight gradient is computed transposed, dW^T[(t,c), o], so that the long
-// dimension taps*Cin fills the 128 TMEM lanes and Cout <= 256 is one N tile).
+// The three products of a convolution layer are the GEMMs listed in conv.cu, tiled here
+// as (M x N output tile, K in stages of 64 bf16):
+//   forward      M = pixels,     N = Cout, K = taps*Cin    A, B K-major
+//   data grad    M = pixels,     N = Cin,  K = taps*Cout   A, B K-major
+//   weight grad  M = taps*Cin,   N = Cout, K = pixels      A, B MN-major, K split in chunks
+// (the weight gradient is formed transposed, dW^T[(t,c), o], so that the long dimension
+// taps*Cin fills the 128 TMEM lanes; its partial tiles are added with FP32 atomics).
 //
-// One CTA of 128 threads owns a 128 x bn tile (bn a multiple of 16, at most 256).
-// All threads gather operand tiles with 16-byte cp.async copies (zero-filled outside the
-// image, the channel range and the pixel range) straight into the canonical
-// no-swizzle core-matrix layout: vector v of a tile lands at byte 16 v, which makes the
-// shared-memory writes conflict-free and the global reads of 8 threads one 128-byte row.
-//   K-major tile (R rows x 64 k): core matrix (rows 8i..8i+7, k 8j..8j+7) at (8 i + j) 128;
-//     descriptor LBO (next core matrix along K) = 128 B, SBO (next 8 rows) = 1024 B.
-//   MN-major tile: core matrix (mn 8i.., k 8j..) at (j R/8 + i) 128 with one k per
-//     16-byte row; LBO (along K) = 16 R B, SBO (along MN) = 128 B.
-// A four-stage ring overlaps the gathers of stages kt+1..kt+3 with the MMAs of stage kt;
-// thread 0 issues four 128 x bn x 16 MMAs per stage and commits them to the stage's
-// mbarrier, which every thread waits on (bounded) before refilling that stage.  The
-// epilogue reads the accumulator rows with tcgen05.ld (warp w owns lanes 32w..32w+31,
-// one output row per thread) and applies bias / ReLU / bf16 rounding, or adds the
-// partial weight gradient with FP32 atomics.
+// Persistent, warp-specialised CTA (one per SM, 13 warps), over tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...:
+//   warps 0-7   producers: gather the operand tiles of each K stage with 16-byte cp.async
+//               copies (zero-filled outside the image, the channels and the pixel range)
+//               into a ring of shared-memory stages, then signal the stage's `full`
+//               mbarrier once their copies have landed (two stages kept in flight per
+//               thread before that wait);
+//   warp 8      one thread issues four 128 x bn x 16 MMAs per stage and commits them to
+//               the stage's `empty` mbarrier (which frees it for the producers), and after
+//               a tile's last stage to the `tfull` mbarrier of its accumulator buffer;
+//   warps 9-12  epilogue: read the finished accumulator rows with tcgen05.ld (warp w owns
+//               TMEM lanes 32 (w mod 4) .. +31, one output row per thread), apply bias /
+//               ReLU / rounding or the atomic add, and release the buffer (`tempty`).
+// Two accumulator buffers of bn TMEM columns let the MMAs of tile i+1 run while the
+// epilogue drains tile i.  Every wait is bounded; a wait that gives up sets a CTA-wide
+// abort flag (all roles leave their loops) and a global flag read by rbgs_conv_check.
+//
+// Shared-memory operand layouts (bf16, one stage = A 128 x 64 then B bn x 64):
+//   K-major, 128-byte swizzle: row r of the tile is 128 bytes (64 k); its 16-byte chunk
+//     c sits at chunk position c ^ (r mod 8) inside the 8-row, 1024-byte atom of rows
+//     8 (r / 8) ..; descriptor SBO = 1024 B, LBO unused, K step of 16 = +32 bytes.
+//   MN-major, 128-byte swizzle (weight-grad A): atoms of 8 k-rows x 64 mn; within an atom
+//     k-row q holds 128 bytes of mn values with chunk c at position c ^ q; the two mn
+//     atoms of a k group are 1024 B apart (LBO), k groups 2048 B apart (SBO).
+//   MN-major, no swizzle (weight-grad B): core matrix (mn group i, k group j) = 8 k-rows of
+//     16 bytes at (j bn/8 + i) 128; LBO (next k group) = 16 bn B, SBO (next mn group) = 128 B.
+// The producer mapping puts the 8 threads of each quarter-warp on 8 different rows of
+// one chunk column, so their 16-byte writes fall in 8 distinct bank groups.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -38,15 +51,44 @@ __device__ int g_conv_wait_failed;
 
 namespace {
 
-constexpr int UM = 128;        // tile rows = TMEM lanes
-constexpr int UK = 64;         // K per stage: 128 bytes of bf16 per row
-constexpr int USTAGES = 4;
-constexpr int UTHREADS = 128;
-constexpr uint32_t kUmmaPolls = 1u << 22;
+constexpr int UM = 128;              // tile rows = TMEM lanes
+constexpr int UK = 64;               // K per stage: 128 bytes of bf16 per row
+constexpr int kProducers = 256;      // warps 0-7
+constexpr int kMmaWarp = 8;
+constexpr int kEpiWarp0 = 9;         // warps 9-12
+constexpr int kThreads = 416;
+constexpr int kMaxStages = 10;
+constexpr int kLag = 2;              // stages in flight per producer before it signals
+constexpr uint32_t kPolls = 1u << 22;
 constexpr int kMaxBn = 256;
-constexpr size_t kMaxSmem = (size_t)USTAGES * (UM + kMaxBn) * UK * 2;
+constexpr uint32_t kRingBudget = 200 * 1024;
+constexpr size_t kMaxSmem = kRingBudget + 1024;
 
 enum UMode { U_FWD = 0, U_BWD_DATA = 1, U_BWD_WEIGHT = 2 };
+
+// Division of 0 <= n < 2^31 by an invariant d >= 1 with a multiply-high and a shift
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", 1994):
+// with l = ceil(log2 d) and p = 31 + l, mul = ceil(2^p / d) < 2^32 and n / d =
+// (n mul) >> p, since n (mul d - 2^p) < 2^31 d <= 2^p.
+struct FastDiv {
+    uint32_t d, mul, shr;
+};
+
+FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f{d, 0u, 0u};
+    if (d > 1) {
+        uint32_t l = 0;
+        while ((1ull << l) < d) ++l;
+        const uint32_t p = 31 + l;
+        f.mul = (uint32_t)(((1ull << p) + d - 1) / d);
+        f.shr = p - 32;
+    }
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
+    return f.d == 1 ? n : (__umulhi(n, f.mul) >> f.shr);
+}
 
 struct UArgs {
     const uint16_t *X;   // NHWC bf16 activations
@@ -56,15 +98,17 @@ struct UArgs {
     void *out;
     int H, W, Cin, Cout, ks;
     int relu, y_fp32, accumulate;
-    long M, N, K;        // GEMM sizes
-    int bn;              // N tile
-    long k_chunk;        // weight grad: pixels per CTA (multiple of UK)
-    uint32_t tmem_cols;  // power of two >= max(32, bn)
+    int M, N, K;         // GEMM sizes
+    int bn, stages;
+    int m_tiles, n_tiles, k_chunk, num_tiles;
+    int log2_groups;     // weight grad: log2(bn / 8)
+    uint32_t tmem_cols;  // power of two >= max(32, 2 bn)
+    FastDiv div_w, div_hw;
 };
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
                  : "memory");
 }
 
@@ -75,17 +119,21 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor, no swizzle: start address, leading (K-direction) and
-// stride (MN-direction) byte offsets between core matrices, descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor: start address, leading / stride byte offsets,
+// descriptor version 1, swizzle mode (0 none, 2 = 128-byte).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t swizzle) {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)swizzle << 61);
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, major-ness of each
@@ -126,37 +174,337 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
+// Bounded wait that also gives up as soon as another role has aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    for (uint32_t q = 0; q < kPolls; ++q) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((q & 63u) == 63u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicOr(&g_conv_wait_failed, 1);
+    return false;
+}
+
+struct Tile {
+    int m0, n0, kbeg, kend, KT;
+};
+
+template <int MODE>
+__device__ __forceinline__ Tile decode_tile(const UArgs &a, int tile) {
+    Tile t;
+    int rest = tile;
+    t.kbeg = 0;
+    t.kend = a.K;
+    if (MODE == U_BWD_WEIGHT) {
+        const int per = a.m_tiles * a.n_tiles;
+        const int chunk = tile / per;
+        rest = tile - chunk * per;
+        t.kbeg = chunk * a.k_chunk;
+        t.kend = min(a.K, t.kbeg + a.k_chunk);
+    }
+    const int mt = rest / a.n_tiles;
+    t.m0 = mt * UM;
+    t.n0 = (rest - mt * a.n_tiles) * a.bn;
+    t.KT = (t.kend - t.kbeg + UK - 1) / UK;
+    return t;
+}
+
+// ------------------------------------------------------------------ producers
+template <int MODE>
+__device__ void produce(const UArgs &a, uint32_t sbase, uint32_t stage_bytes, uint64_t *full_bar,
+                        uint64_t *empty_bar, volatile int *abort_flag) {
+    const int ptid = threadIdx.x;  // 0..255
+    const int bn = a.bn, S = a.stages;
+    const uint32_t a_bytes = UM * UK * 2;
+    const int b_vecs = bn * 8;
+    const int pad = a.ks / 2;
+    const uint32_t HW = (uint32_t)a.H * (uint32_t)a.W;
+    uint32_t s = 0, ph = 0, s_arr = 0;
+    int issued = 0, arrived = 0;
+    bool live = true;
+
+    if (MODE != U_BWD_WEIGHT) {
+        // K-major A and B: this thread fills rows 8 (rh0 + 4 it) + row_lo, chunk kc.
+        const int row_lo = ptid & 7, kc = (ptid >> 3) & 7, rh0 = ptid >> 6;
+        const uint32_t sw = (uint32_t)(row_lo * 128 + ((kc ^ row_lo) << 4));
+        const int CK = MODE == U_FWD ? a.Cin : a.Cout;
+        const uint16_t *src = MODE == U_FWD ? a.X : a.G;
+        const int t_init = (kc * 8) / CK, ch_init = kc * 8 - t_init * CK;
+        const int tx_init = t_init % a.ks, ty_init = t_init / a.ks;
+        for (int tile = blockIdx.x; tile < a.num_tiles && live; tile += gridDim.x) {
+            const Tile T = decode_tile<MODE>(a, tile);
+            int pyx[4];
+            long mbase[4];
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                const int m = T.m0 + (rh0 + 4 * it) * 8 + row_lo;
+                if (m < a.M) {
+                    const uint32_t r = (uint32_t)m - fdiv((uint32_t)m, a.div_hw) * HW;
+                    const uint32_t y = fdiv(r, a.div_w);
+                    pyx[it] = (int)((y << 16) | (r - y * (uint32_t)a.W));
+                    mbase[it] = (long)m * CK;
+                } else {
+                    pyx[it] = -1;
+                    mbase[it] = 0;
+                }
+            }
+            int ch = ch_init, tx = tx_init, ty = ty_init;
+            for (int kt = 0; kt < T.KT; ++kt) {
+                if (!wait_or_abort(&empty_bar[s], ph ^ 1u, abort_flag)) {
+                    live = false;
+                    break;
+                }
+                const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
+                const bool kval = ty < a.ks;  // tap index < taps
+                int dy = ty - pad, dx = tx - pad;
+                if (MODE == U_BWD_DATA) dy = -dy, dx = -dx;
+                const long delta = ((long)dy * a.W + dx) * CK + ch;
+#pragma unroll
+                for (int it = 0; it < 4; ++it) {
+                    const int yx = pyx[it];
+                    const int y = (yx >> 16) + dy, x = (yx & 0xFFFF) + dx;
+                    const bool ok = kval && yx >= 0 && y >= 0 && y < a.H && x >= 0 && x < a.W;
+                    cp_async16(sa + (uint32_t)(rh0 + 4 * it) * 1024u + sw, ok ? src + mbase[it] + delta : src, ok);
+                }
+#pragma unroll
+                for (int it = 0; it < kMaxBn * 8 / kProducers; ++it) {
+                    const int v = ptid + kProducers * it;
+                    if (v >= b_vecs) break;
+                    const int n = T.n0 + (rh0 + 4 * it) * 8 + row_lo;
+                    const bool ok = kval && n < a.N;
+                    const uint16_t *p = a.Wt;
+                    if (ok) {
+                        if (MODE == U_FWD)
+                            p = a.Wt + (long)n * a.K + kt * UK + kc * 8;  // Wt[o][t][c], k = t Cin + c
+                        else
+                            p = a.Wt + ((long)(ty * a.ks + tx) * a.Cin + n) * a.Cout + ch;  // Wt_t[t][c][o]
+                    }
+                    cp_async16(sb + (uint32_t)(rh0 + 4 * it) * 1024u + sw, p, ok);
+                }
+                cp_async_commit();
+                ++issued;
+                if (issued > kLag) {
+                    cp_async_wait<kLag>();
+                    fence_proxy_async_smem();
+                    mbar_arrive(&full_bar[s_arr]);
+                    ++arrived;
+                    if (++s_arr == (uint32_t)S) s_arr = 0;
+                }
+                ch += UK;
+                while (ch >= CK) {
+                    ch -= CK;
+                    if (++tx == a.ks) tx = 0, ++ty;
+                }
+                if (++s == (uint32_t)S) s = 0, ph ^= 1u;
+            }
+        }
+    } else {
+        // MN-major A (128B swizzle): mn group ig of the tile, k rows 8 (j0 + 2 it) + kr.
+        const int kr = ptid & 7, ig = (ptid >> 3) & 15, j0 = ptid >> 7;
+        const uint32_t a_sw = (uint32_t)((ig >> 3) * 1024 + kr * 128 + (((ig & 7) ^ kr) << 4));
+        const int gmask = (1 << a.log2_groups) - 1;
+        for (int tile = blockIdx.x; tile < a.num_tiles && live; tile += gridDim.x) {
+            const Tile T = decode_tile<MODE>(a, tile);
+            const int m = T.m0 + ig * 8;  // (t, c) of this thread's 8 rows
+            const bool mval = m < a.M;
+            int dy = 0, dx = 0, c = 0;
+            if (mval) {
+                const int t = m / a.Cin;
+                c = m - t * a.Cin;
+                dy = t / a.ks - pad;
+                dx = t % a.ks - pad;
+            }
+            const long shift = ((long)dy * a.W + dx) * a.Cin + c;
+            for (int kt = 0; kt < T.KT; ++kt) {
+                if (!wait_or_abort(&empty_bar[s], ph ^ 1u, abort_flag)) {
+                    live = false;
+                    break;
+                }
+                const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
+                const int k0 = T.kbeg + kt * UK;
+#pragma unroll
+                for (int it = 0; it < 4; ++it) {
+                    const int p = k0 + (j0 + 2 * it) * 8 + kr;
+                    bool ok = mval && p < T.kend;
+                    if (ok) {
+                        const uint32_t r = (uint32_t)p - fdiv((uint32_t)p, a.div_hw) * HW;
+                        const int y = (int)fdiv(r, a.div_w);
+                        const int x = (int)r - y * a.W;
+                        ok = y + dy >= 0 && y + dy < a.H && x + dx >= 0 && x + dx < a.W;
+                    }
+                    cp_async16(sa + (uint32_t)(j0 + 2 * it) * 2048u + a_sw,
+                               ok ? a.X + (long)p * a.Cin + shift : a.X, ok);
+                }
+#pragma unroll
+                for (int it = 0; it < kMaxBn * 8 / kProducers; ++it) {
+                    const int v = ptid + kProducers * it;
+                    if (v >= b_vecs) break;
+                    const int g = v >> 3;
+                    const int p = k0 + (g >> a.log2_groups) * 8 + (v & 7);
+                    const int n = T.n0 + (g & gmask) * 8;
+                    const bool ok = p < T.kend && n < a.N;
+                    cp_async16(sb + (uint32_t)v * 16u, ok ? a.G + (long)p * a.Cout + n : a.G, ok);
+                }
+                cp_async_commit();
+                ++issued;
+                if (issued > kLag) {
+                    cp_async_wait<kLag>();
+                    fence_proxy_async_smem();
+                    mbar_arrive(&full_bar[s_arr]);
+                    ++arrived;
+                    if (++s_arr == (uint32_t)S) s_arr = 0;
+                }
+                if (++s == (uint32_t)S) s = 0, ph ^= 1u;
+            }
+        }
+    }
+    cp_async_wait<0>();
+    fence_proxy_async_smem();
+    while (arrived < issued) {
+        mbar_arrive(&full_bar[s_arr]);
+        ++arrived;
+        if (++s_arr == (uint32_t)S) s_arr = 0;
+    }
+}
+
+// ------------------------------------------------------------------ MMA issuer
+template <int MODE>
+__device__ void issue_mmas(const UArgs &a, uint32_t sbase, uint32_t stage_bytes, uint32_t tmem,
+                           uint64_t *full_bar, uint64_t *empty_bar, uint64_t *tfull_bar, uint64_t *tempty_bar,
+                           volatile int *abort_flag) {
+    constexpr bool MN = MODE == U_BWD_WEIGHT;
+    const int bn = a.bn, S = a.stages;
+    const uint32_t a_bytes = UM * UK * 2;
+    const uint32_t idesc = instr_desc(UM, bn, MN ? 1 : 0, MN ? 1 : 0);
+    uint32_t s = 0, ph = 0;
+    int local = 0;
+    for (int tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x, ++local) {
+        const Tile T = decode_tile<MODE>(a, tile);
+        const int buf = local & 1;
+        if (!wait_or_abort(&tempty_bar[buf], (((uint32_t)local >> 1) & 1u) ^ 1u, abort_flag)) return;
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(buf * bn);
+        for (int kt = 0; kt < T.KT; ++kt) {
+            if (!wait_or_abort(&full_bar[s], ph, abort_flag)) return;
+            tc_fence_after();
+            const uint32_t sa = sbase + s * stage_bytes, sb = sa + a_bytes;
+#pragma unroll
+            for (int kk = 0; kk < UK / 16; ++kk) {
+                uint64_t ad, bd;
+                if (!MN) {
+                    ad = smem_desc(sa + kk * 32, 16, 1024, 2);
+                    bd = smem_desc(sb + kk * 32, 16, 1024, 2);
+                } else {
+                    ad = smem_desc(sa + kk * 4096, 1024, 2048, 2);
+                    bd = smem_desc(sb + kk * (uint32_t)bn * 32u, (uint32_t)bn * 16u, 128, 0);
+                }
+                umma_bf16(acc, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit(&empty_bar[s]);
+            if (++s == (uint32_t)S) s = 0, ph ^= 1u;
+        }
+        umma_commit(&tfull_bar[buf]);
+    }
+}
+
+// ------------------------------------------------------------------ epilogue
+template <int MODE>
+__device__ void drain(const UArgs &a, uint32_t tmem, uint64_t *tfull_bar, uint64_t *tempty_bar,
+                      volatile int *abort_flag) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int bn = a.bn;
+    int local = 0;
+    for (int tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x, ++local) {
+        const Tile T = decode_tile<MODE>(a, tile);
+        const int buf = local & 1;
+        // warp-uniform: the tcgen05.ld below needs every lane of the warp
+        const bool ok = wait_or_abort(&tfull_bar[buf], ((uint32_t)local >> 1) & 1u, abort_flag);
+        if (!__all_sync(0xffffffffu, ok)) return;
+        tc_fence_after();
+        const int m = T.m0 + q * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < bn; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * bn + c0), r);
+            if (m >= a.M) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int n = T.n0 + c0 + h * 8;
+                if (n >= a.N) continue;  // N is a multiple of 8: all 8 columns or none
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[h * 8 + e]);
+                if (MODE == U_FWD) {
+                    if (a.bias) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[e] += a.bias[n + e];
+                    }
+                    if (a.relu) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[e] = fmaxf(v[e], 0.f);
+                    }
+                    const long o = (long)m * a.N + n;
+                    if (a.y_fp32) {
+                        float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(a.out) + o);
+                        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    } else {
+                        *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(a.out) + o) =
+                            make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                       pack_bf16(v[6], v[7]));
+                    }
+                } else if (MODE == U_BWD_DATA) {
+                    float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(a.out) + (long)m * a.N + n);
+                    float4 p0 = make_float4(v[0], v[1], v[2], v[3]), p1 = make_float4(v[4], v[5], v[6], v[7]);
+                    if (a.accumulate) {
+                        const float4 q0 = dst[0], q1 = dst[1];
+                        p0.x += q0.x, p0.y += q0.y, p0.z += q0.z, p0.w += q0.w;
+                        p1.x += q1.x, p1.y += q1.y, p1.z += q1.z, p1.w += q1.w;
+                    }
+                    dst[0] = p0;
+                    dst[1] = p1;
+                } else {
+                    float *dw = reinterpret_cast<float *>(a.out);  // dW[o][t][c] = dW[n M + m]
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) atomicAdd(dw + (long)(n + e) * a.M + m, v[e]);
+                }
+            }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty_bar[buf]);
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 template <int MODE>
-__global__ void __launch_bounds__(UTHREADS) conv_umma_kernel(UArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mma_bar[USTAGES];
+__global__ void __launch_bounds__(kThreads, 1) conv_umma_kernel(const UArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tfull_bar[2], tempty_bar[2];
     __shared__ uint32_t tmem_slot;
-    constexpr bool MN = MODE == U_BWD_WEIGHT;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bn = a.bn;
-    const uint32_t a_bytes = UM * UK * 2, b_bytes = (uint32_t)bn * UK * 2;
-    const uint32_t stage_bytes = a_bytes + b_bytes;
-    const uint32_t sbase = smem_addr(smem);
-    const long m0 = (long)blockIdx.x * UM, n0 = (long)blockIdx.y * bn;
-    long kbeg = 0, kend = a.K;
-    if (MODE == U_BWD_WEIGHT) {
-        kbeg = (long)blockIdx.z * a.k_chunk;
-        kend = kbeg + a.k_chunk < a.K ? kbeg + a.k_chunk : a.K;
-    }
-    const int KT = kend > kbeg ? (int)((kend - kbeg + UK - 1) / UK) : 0;
-    const int pad = a.ks / 2;
-    const long HW = (long)a.H * a.W;
+    __shared__ int abort_word;
+    volatile int *abort_flag = &abort_word;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t stage_bytes = (uint32_t)(UM + a.bn) * UK * 2;
+    const uint32_t sbase = (smem_addr(smem_raw) + 1023u) & ~1023u;  // swizzle atoms are 1024-aligned
 
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_addr(&tmem_slot)),
                      "r"(a.tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) {
-        for (int s = 0; s < USTAGES; ++s) mbar_init(&mma_bar[s], 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(&full_bar[s], kProducers);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull_bar[b], 1);
+            mbar_init(&tempty_bar[b], 128);
+        }
+        *abort_flag = 0;
         fence_barrier_init();
     }
     tc_fence_before();
@@ -164,231 +512,23 @@ __global__ void __launch_bounds__(UTHREADS) conv_umma_kernel(UArgs a) {
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    // Per-thread constants of the A gather.  K-major A: this thread fills vectors
-    // tid + 128 it (it = 0..7), i.e. rows 8 ((tid >> 6) + 2 it) + (tid & 7) at k chunk
-    // (tid >> 3) & 7.  MN-major A: mn group (tid >> 3) & 15 at k rows 8 it + (tid & 7).
-    int pyx[8];  // K-major: (y << 16 | x) of the row's pixel, -1 past the last pixel
-    int a_dy = 0, a_dx = 0, a_c = 0;
-    bool a_mval = false;
-    if (!MN) {
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-            const long m = m0 + ((tid >> 6) + 2 * it) * 8 + (tid & 7);
-            if (m < a.M) {
-                const int r = (int)(m % HW);
-                pyx[it] = ((r / a.W) << 16) | (r % a.W);
-            } else {
-                pyx[it] = -1;
-            }
-        }
-    } else {
-        const long m = m0 + ((tid >> 3) & 15) * 8;  // (t, c) index of the thread's 8 rows
-        a_mval = m < a.M;
-        if (a_mval) {
-            const int t = (int)(m / a.Cin);
-            a_c = (int)(m - (long)t * a.Cin);
-            a_dy = t / a.ks - pad;
-            a_dx = t % a.ks - pad;
-        }
+    if (warp < kMmaWarp) {
+        produce<MODE>(a, sbase, stage_bytes, full_bar, empty_bar, abort_flag);
+    } else if (warp == kMmaWarp) {
+        if ((threadIdx.x & 31) == 0)
+            issue_mmas<MODE>(a, sbase, stage_bytes, tmem, full_bar, empty_bar, tfull_bar, tempty_bar, abort_flag);
+    } else if (warp >= kEpiWarp0) {
+        drain<MODE>(a, tmem, tfull_bar, tempty_bar, abort_flag);
     }
 
-    auto load_tile = [&](int kt, int s) {
-        const uint32_t sa = sbase + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
-        const long k0 = kbeg + (long)kt * UK;
-        if (!MN) {
-            const long k = k0 + ((tid >> 3) & 7) * 8;
-            const int CK = MODE == U_FWD ? a.Cin : a.Cout;
-            const uint16_t *src = MODE == U_FWD ? a.X : a.G;
-            const bool kval = k < a.K;
-            int dy = 0, dx = 0, ch = 0;
-            if (kval) {
-                const int t = (int)(k / CK);
-                ch = (int)(k - (long)t * CK);
-                dy = t / a.ks - pad;
-                dx = t % a.ks - pad;
-                if (MODE == U_BWD_DATA) dy = -dy, dx = -dx;
-            }
-#pragma unroll
-            for (int it = 0; it < 8; ++it) {
-                const int yx = pyx[it];
-                const int y = (yx >> 16) + dy, x = (yx & 0xFFFF) + dx;
-                const bool ok = kval && yx >= 0 && y >= 0 && y < a.H && x >= 0 && x < a.W;
-                const long m = m0 + ((tid >> 6) + 2 * it) * 8 + (tid & 7);
-                const uint16_t *p = ok ? src + ((m + (long)dy * a.W + dx) * CK + ch) : src;
-                cp_async16(sa + (uint32_t)(tid + it * UTHREADS) * 16, p, ok);
-            }
-            for (int v = tid; v < bn * 8; v += UTHREADS) {
-                const long n = n0 + (v >> 6) * 8 + (v & 7);
-                const long kb = k0 + ((v >> 3) & 7) * 8;
-                const bool ok = n < a.N && kb < a.K;
-                const uint16_t *p = a.Wt;
-                if (ok) {
-                    if (MODE == U_FWD) {
-                        p = a.Wt + n * a.K + kb;  // Wt[o][t][c], k = t Cin + c
-                    } else {
-                        const int t = (int)(kb / a.Cout);
-                        const int o = (int)(kb - (long)t * a.Cout);
-                        p = a.Wt + ((long)t * a.Cin + n) * a.Cout + o;  // Wt_t[t][c][o]
-                    }
-                }
-                cp_async16(sb + (uint32_t)v * 16, p, ok);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const long p = k0 + j * 8 + (tid & 7);
-                bool ok = a_mval && p < kend;
-                const uint16_t *q = a.X;
-                if (ok) {
-                    const int r = (int)(p % HW);
-                    const int y = r / a.W + a_dy, x = r % a.W + a_dx;
-                    ok = y >= 0 && y < a.H && x >= 0 && x < a.W;
-                    if (ok) q = a.X + (p + (long)a_dy * a.W + a_dx) * a.Cin + a_c;
-                }
-                cp_async16(sa + (uint32_t)(tid + j * UTHREADS) * 16, q, ok);
-            }
-            const int groups = bn >> 3;
-            for (int v = tid; v < bn * 8; v += UTHREADS) {
-                const int g = v >> 3;
-                const long p = k0 + (g / groups) * 8 + (v & 7);
-                const long n = n0 + (g % groups) * 8;
-                const bool ok = p < kend && n < a.N;
-                cp_async16(sb + (uint32_t)v * 16, ok ? a.G + p * a.Cout + n : a.G, ok);
-            }
-        }
-    };
-
-    const uint32_t idesc = instr_desc(UM, bn, MN ? 1 : 0, MN ? 1 : 0);
-    const uint32_t a_lbo = MN ? UM * 16 : 128, a_sbo = MN ? 128 : 1024;
-    const uint32_t b_lbo = MN ? (uint32_t)bn * 16 : 128, b_sbo = MN ? 128 : 1024;
-    const uint32_t a_kstep = MN ? UM * 32 : 256, b_kstep = MN ? (uint32_t)bn * 32 : 256;
-    bool waits_ok = true;
-
-#pragma unroll 1
-    for (int kt = 0; kt < USTAGES - 1; ++kt) {
-        if (kt < KT) load_tile(kt, kt);
-        cp_async_commit();
-    }
-#pragma unroll 1
-    for (int kt = 0; kt < KT; ++kt) {
-        const int s = kt % USTAGES;
-        cp_async_wait<USTAGES - 2>();
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t sa = sbase + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
-#pragma unroll
-            for (int kk = 0; kk < UK / 16; ++kk) {
-                const uint64_t ad = smem_desc(sa + kk * a_kstep, a_lbo, a_sbo);
-                const uint64_t bd = smem_desc(sb + kk * b_kstep, b_lbo, b_sbo);
-                umma_bf16(tmem, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-            }
-            umma_commit(&mma_bar[s]);
-        }
-        const int nt = kt + USTAGES - 1;
-        if (nt < KT) {
-            if (kt >= 1) {
-                const int j = kt - 1;  // the stage being refilled last held tile kt - 1
-                if (!mbar_wait_bounded(&mma_bar[j % USTAGES], (uint32_t)(j / USTAGES) & 1u, kUmmaPolls))
-                    waits_ok = false;
-            }
-            load_tile(nt, nt % USTAGES);
-        }
-        cp_async_commit();
-    }
-    cp_async_wait<0>();
-    if (KT > 0) {
-        const int j = KT - 1;  // its commit arrives once every MMA of the CTA has completed
-        if (!mbar_wait_bounded(&mma_bar[j % USTAGES], (uint32_t)(j / USTAGES) & 1u, kUmmaPolls))
-            waits_ok = false;
-    }
-    if (!waits_ok) atomicOr(&g_conv_wait_failed, 1);
-    tc_fence_after();
-
-    // ---- epilogue: thread (warp w, lane l) owns output row 32 w + l
-    const long m = m0 + warp * 32 + lane;
-#pragma unroll 1
-    for (int c0 = 0; c0 < bn; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-        if (m >= a.M || KT == 0 || !waits_ok) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const long n = n0 + c0 + h * 8;
-            if (n >= a.N) continue;  // N is a multiple of 8: all 8 columns or none
-            float v[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[h * 8 + e]);
-            if (MODE == U_FWD) {
-                if (a.bias) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] += a.bias[n + e];
-                }
-                if (a.relu) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = fmaxf(v[e], 0.f);
-                }
-                if (a.y_fp32) {
-                    float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(a.out) + m * a.N + n);
-                    o[0] = make_float4(v[0], v[1], v[2], v[3]);
-                    o[1] = make_float4(v[4], v[5], v[6], v[7]);
-                } else {
-                    *reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(a.out) + m * a.N + n) =
-                        make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                                   pack_bf16(v[6], v[7]));
-                }
-            } else if (MODE == U_BWD_DATA) {
-                float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(a.out) + m * a.N + n);
-                float4 p0 = make_float4(v[0], v[1], v[2], v[3]), p1 = make_float4(v[4], v[5], v[6], v[7]);
-                if (a.accumulate) {
-                    const float4 q0 = o[0], q1 = o[1];
-                    p0.x += q0.x, p0.y += q0.y, p0.z += q0.z, p0.w += q0.w;
-                    p1.x += q1.x, p1.y += q1.y, p1.z += q1.z, p1.w += q1.w;
-                }
-                o[0] = p0;
-                o[1] = p1;
-            } else {
-                float *dw = reinterpret_cast<float *>(a.out);  // dW[o][t][c] = dW[n M + m]
-#pragma unroll
-                for (int e = 0; e < 8; ++e) atomicAdd(dw + (n + e) * a.M + m, v[e]);
-            }
-        }
-    }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
+    if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols)
                      : "memory");
 }
 
-// N tile: the fewest tiles of at most 256 columns, each a multiple of 16.
-int pick_bn(long N) {
-    const long tiles = (N + kMaxBn - 1) / kMaxBn;
-    const long per = (N + tiles - 1) / tiles;
-    return (int)((per + 15) / 16 * 16);
-}
-
-uint32_t tmem_columns(int bn) {
-    uint32_t c = 32;
-    while ((int)c < bn) c <<= 1;
-    return c;
-}
-
-template <int MODE>
-rbgs_status launch(UArgs a, dim3 grid, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        RBGS_CUDA(cudaFuncSetAttribute(conv_umma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kMaxSmem));
-        attr_set = true;
-    }
-    const size_t smem = (size_t)USTAGES * (UM + a.bn) * UK * 2;
-    conv_umma_kernel<MODE><<<grid, UTHREADS, smem, s>>>(a);
-    RBGS_LAUNCH_CHECK();
-    return RBGS_OK;
-}
-
+// ------------------------------------------------------------------ host side
 int sm_count() {
     static int sms = 0;
     if (!sms) {
@@ -400,49 +540,111 @@ int sm_count() {
     return sms;
 }
 
+// N tile for K-major B: the fewest tiles of at most 256 columns, each a multiple of 16.
+int pick_bn(int N) {
+    const int tiles = (N + kMaxBn - 1) / kMaxBn;
+    const int per = (N + tiles - 1) / tiles;
+    return (per + 15) / 16 * 16;
+}
+
+// N tile for the weight gradient's MN-major B: a power of two in [16, 256].
+int pick_bn_pow2(int N) {
+    int bn = 16;
+    while (bn < N && bn < kMaxBn) bn <<= 1;
+    return bn;
+}
+
+void finish_args(UArgs &a, int B) {
+    a.stages = (int)(kRingBudget / ((uint32_t)(UM + a.bn) * UK * 2));
+    if (a.stages > kMaxStages) a.stages = kMaxStages;
+    uint32_t cols = 32;
+    while ((int)cols < 2 * a.bn) cols <<= 1;
+    a.tmem_cols = cols;
+    a.m_tiles = (a.M + UM - 1) / UM;
+    a.n_tiles = (a.N + a.bn - 1) / a.bn;
+    a.div_w = make_fastdiv((uint32_t)a.W);
+    a.div_hw = make_fastdiv((uint32_t)a.H * (uint32_t)a.W);
+    (void)B;
+}
+
+template <int MODE>
+rbgs_status launch(const UArgs &a, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        RBGS_CUDA(cudaFuncSetAttribute(conv_umma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kMaxSmem));
+        attr_set = true;
+    }
+    const size_t smem = (size_t)a.stages * (UM + a.bn) * UK * 2 + 1024;
+    const int grid = a.num_tiles < sm_count() ? a.num_tiles : sm_count();
+    conv_umma_kernel<MODE><<<grid, kThreads, smem, s>>>(a);
+    RBGS_LAUNCH_CHECK();
+    return RBGS_OK;
+}
+
+bool sizes_fit(int B, int H, int W) { return (long)B * H * W < (1L << 31) - UK; }
+
 }  // namespace
 
 rbgs_status umma_conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y, int B, int H,
                               int W, int Cin, int Cout, int ks, int relu, int y_fp32, cudaStream_t s) {
+    if (!sizes_fit(B, H, W)) {
+        set_error("tcgen05 convolution: at most 2^31 - 64 pixels");
+        return RBGS_EINVAL;
+    }
     UArgs a{};
     a.X = X, a.Wt = Wt, a.bias = bias, a.out = Y;
     a.H = H, a.W = W, a.Cin = Cin, a.Cout = Cout, a.ks = ks, a.relu = relu, a.y_fp32 = y_fp32;
-    a.M = (long)B * H * W, a.N = Cout, a.K = (long)ks * ks * Cin;
-    a.bn = pick_bn(a.N), a.tmem_cols = tmem_columns(a.bn);
-    dim3 grid((unsigned)((a.M + UM - 1) / UM), (unsigned)((a.N + a.bn - 1) / a.bn), 1);
-    return launch<U_FWD>(a, grid, s);
+    a.M = B * H * W, a.N = Cout, a.K = ks * ks * Cin;
+    a.bn = pick_bn(a.N);
+    finish_args(a, B);
+    a.num_tiles = a.m_tiles * a.n_tiles;
+    return launch<U_FWD>(a, s);
 }
 
 rbgs_status umma_conv_backward_data(const uint16_t *Wtt, const uint16_t *G, float *dX, int B, int H, int W,
                                     int Cin, int Cout, int ks, int accumulate, cudaStream_t s) {
+    if (!sizes_fit(B, H, W)) {
+        set_error("tcgen05 convolution: at most 2^31 - 64 pixels");
+        return RBGS_EINVAL;
+    }
     UArgs a{};
     a.Wt = Wtt, a.G = G, a.out = dX;
     a.H = H, a.W = W, a.Cin = Cin, a.Cout = Cout, a.ks = ks, a.accumulate = accumulate;
-    a.M = (long)B * H * W, a.N = Cin, a.K = (long)ks * ks * Cout;
-    a.bn = pick_bn(a.N), a.tmem_cols = tmem_columns(a.bn);
-    dim3 grid((unsigned)((a.M + UM - 1) / UM), (unsigned)((a.N + a.bn - 1) / a.bn), 1);
-    return launch<U_BWD_DATA>(a, grid, s);
+    a.M = B * H * W, a.N = Cin, a.K = ks * ks * Cout;
+    a.bn = pick_bn(a.N);
+    finish_args(a, B);
+    a.num_tiles = a.m_tiles * a.n_tiles;
+    return launch<U_BWD_DATA>(a, s);
 }
 
 rbgs_status umma_conv_backward_weight(const uint16_t *X, const uint16_t *G, float *dW, int B, int H, int W,
                                       int Cin, int Cout, int ks, cudaStream_t s) {
+    if (!sizes_fit(B, H, W)) {
+        set_error("tcgen05 convolution: at most 2^31 - 64 pixels");
+        return RBGS_EINVAL;
+    }
     UArgs a{};
     a.X = X, a.G = G, a.out = dW;
     a.H = H, a.W = W, a.Cin = Cin, a.Cout = Cout, a.ks = ks;
-    a.M = (long)ks * ks * Cin, a.N = Cout, a.K = (long)B * H * W;
-    a.bn = pick_bn(a.N), a.tmem_cols = tmem_columns(a.bn);
-    const long tiles = ((a.M + UM - 1) / UM) * ((a.N + a.bn - 1) / a.bn);
-    // split the pixels so that the grid covers about two waves of the SMs
-    long chunks = (2L * sm_count() + tiles - 1) / tiles;
-    const long max_chunks = (a.K + UK - 1) / UK;
+    a.M = ks * ks * Cin, a.N = Cout, a.K = B * H * W;
+    a.bn = pick_bn_pow2(a.N);
+    int lg = 0;
+    while ((8 << lg) < a.bn) ++lg;
+    a.log2_groups = lg;
+    finish_args(a, B);
+    // split the pixels so that about two tiles fall to each SM
+    const int mn_tiles = a.m_tiles * a.n_tiles;
+    int chunks = (2 * sm_count() + mn_tiles - 1) / mn_tiles;
+    const int max_chunks = (a.K + 4 * UK - 1) / (4 * UK);  // at least four stages per chunk
     if (chunks > max_chunks) chunks = max_chunks;
     if (chunks < 1) chunks = 1;
-    long chunk = (a.K + chunks - 1) / chunks;
+    int chunk = (a.K + chunks - 1) / chunks;
     chunk = (chunk + UK - 1) / UK * UK;
     a.k_chunk = chunk;
-    chunks = (a.K + chunk - 1) / chunk;
-    dim3 grid((unsigned)((a.M + UM - 1) / UM), (unsigned)((a.N + a.bn - 1) / a.bn), (unsigned)chunks);
-    return launch<U_BWD_WEIGHT>(a, grid, s);
+    chunks = (a.K + chunk - 1) / chunk;  // every chunk non-empty
+    a.num_tiles = mn_tiles * chunks;
+    return launch<U_BWD_WEIGHT>(a, s);
 }
 
 rbgs_status umma_conv_check(cudaStream_t s) {
