@@ -14,8 +14,8 @@
 //   warps 0-7   producers: gather the operand tiles of each K stage with 16-byte cp.async
 //               copies (zero-filled outside the image, the channels and the pixel range)
 //               into a ring of shared-memory stages, then signal the stage's `full`
-//               mbarrier once their copies have landed (two stages kept in flight per
-//               thread before that wait);
+//               mbarrier once their copies have landed (two further stages are issued
+//               before a thread waits for a stage's copies);
 //   warp 8      one thread issues four 128 x bn x 16 MMAs per stage and commits them to
 //               the stage's `empty` mbarrier (which frees it for the producers), and after
 //               a tile's last stage to the `tfull` mbarrier of its accumulator buffer;
@@ -58,8 +58,9 @@ constexpr int kMmaWarp = 8;
 constexpr int kEpiWarp0 = 9;         // warps 9-12
 constexpr int kThreads = 416;
 constexpr int kMaxStages = 10;
-constexpr int kLag = 2;              // stages in flight per producer before it signals
-constexpr uint32_t kPolls = 1u << 22;
+constexpr int kLag = 2;                   // stages in flight per producer before it signals
+constexpr uint32_t kPolls = 4000;          // x kSuspendNs: a wait gives up after about 4 s
+constexpr uint32_t kSuspendNs = 1000000;  // each poll sleeps until the phase completes or 1 ms
 constexpr int kMaxBn = 256;
 constexpr uint32_t kRingBudget = 200 * 1024;
 constexpr size_t kMaxSmem = kRingBudget + 1024;
@@ -174,11 +175,25 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
+// One poll that suspends the thread until the phase with `parity` completes, or until
+// kSuspendNs have passed, instead of spinning.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait that also gives up as soon as another role has aborted.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
     for (uint32_t q = 0; q < kPolls; ++q) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((q & 63u) == 63u && *abort_flag) return false;
+        if (mbar_try_wait_suspend(bar, parity)) return true;
+        if (*abort_flag) return false;
     }
     *abort_flag = 1;
     atomicOr(&g_conv_wait_failed, 1);
