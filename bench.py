@@ -62,7 +62,13 @@ def parse():
     p.add_argument("--eval-sizes", default="1023,4095", help="learned: held-out grid sizes")
     p.add_argument("--eval-fields", type=int, default=2, help="learned: held-out fields per size")
     p.add_argument("--eval-cap", default="2500000,400000", help="learned: sweep cap per solve, per size")
-    p.add_argument("--mode", choices=["grid", "batched", "learned"], default="grid",
+    p.add_argument("--conv-batch", type=int, default=16, help="conv: batch of the layer inputs")
+    p.add_argument("--conv-hw", type=int, default=256, help="conv: level-0 height = width")
+    p.add_argument("--conv-layer", type=int, default=-1, help="conv: one layer index (-1: all 15)")
+    p.add_argument("--conv-op", choices=["all", "fwd", "dgrad", "wgrad"], default="all")
+    p.add_argument("--engine", choices=["tcgen05", "mma_sync", "both"], default="both",
+                   help="conv: convolution engine(s) to time")
+    p.add_argument("--mode", choices=["grid", "batched", "learned", "conv"], default="grid",
                    help="grid: one large grid (default); batched: many uneven problems in one launch")
     p.add_argument("--nprob", type=int, default=512)
     p.add_argument("--sizes", default="63,127,255,511,1023", help="batched: allowed interior sizes")
@@ -337,6 +343,132 @@ def run_batched(args):
     return 0
 
 
+# The learned guess's convolution layers: (Cin, Cout, ksize, level); level l runs at
+# (H / 2^l) x (W / 2^l).  The same table as the network in csrc/unet.cu.
+UNET_LAYERS = ((16, 32, 3, 0), (32, 32, 3, 0), (32, 64, 3, 1), (64, 64, 3, 1), (64, 128, 3, 2),
+               (128, 128, 3, 2), (128, 256, 3, 3), (256, 256, 3, 3), (384, 128, 3, 2), (128, 128, 3, 2),
+               (192, 64, 3, 1), (64, 64, 3, 1), (96, 32, 3, 0), (32, 32, 3, 0), (32, 8, 1, 0))
+
+
+def run_conv(args):
+    """The learned initial guess's convolutions on the tensor cores: for every layer of the
+    U-Net at one training batch (conv_batch x conv_hw^2 at level 0), the forward product
+    (bias, ReLU, bf16 out), the data gradient (not for the input layer) and the weight and
+    bias gradients, through rbgs_conv_forward / rbgs_conv_backward.  A step is one pass over
+    the selected layers and products; value = their FLOP / step time.  Each product is one
+    tcgen05 kernel launch (the data gradient adds a small weight transpose; the bias
+    gradient is a separate call), timed with events on the stream; the roofline entry is
+    the product that takes the most time."""
+    import torch
+
+    import paper_2607_01735_gb300 as rb
+    from paper_2607_01735_gb300 import unet as un
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rb.load_library()
+    stream = torch.cuda.current_stream(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20260701)
+    B, hw = args.conv_batch, args.conv_hw
+    idx = range(len(UNET_LAYERS)) if args.conv_layer < 0 else [args.conv_layer]
+    ops = ("fwd", "dgrad", "wgrad") if args.conv_op == "all" else (args.conv_op,)
+    layers = []
+    for i in idx:
+        cin, cout, k, lev = UNET_LAYERS[i]
+        H = W = hw >> lev
+        x = (torch.randn(B, H, W, cin, generator=gen, device=dev) * 0.5).to(torch.bfloat16)
+        w = (torch.randn(cout, k, k, cin, generator=gen, device=dev) / (k * k * cin) ** 0.5).to(torch.bfloat16)
+        g = (torch.randn(B, H, W, cout, generator=gen, device=dev) * 0.1).to(torch.bfloat16)
+        layers.append(dict(i=i, shape=(B, H, W, cin, cout, k), x=x, w=w, g=g,
+                           bias=torch.zeros(cout, device=dev),
+                           y=torch.empty(B, H, W, cout, dtype=torch.bfloat16, device=dev),
+                           dx=torch.empty(B, H, W, cin, device=dev) if i > 0 else None,
+                           dw=torch.zeros(cout, k, k, cin, device=dev), db=torch.zeros(cout, device=dev),
+                           flop=2.0 * B * H * W * k * k * cin * cout))
+
+    def timed(ev, key, flop, fn):
+        if ev is None:
+            fn()
+            return
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        ev.append((key, flop, e0, e1))
+
+    def step(ev=None):
+        for L in layers:
+            if "fwd" in ops:
+                timed(ev, "fwd", L["flop"], lambda: un.rbgs_conv_forward(L["x"], L["w"], L["bias"], L["y"], relu=True))
+            if "dgrad" in ops and L["dx"] is not None:
+                timed(ev, "dgrad", L["flop"], lambda: un.rbgs_conv_backward(L["x"], L["w"], L["g"], L["dx"], None, None))
+            if "wgrad" in ops:
+                timed(ev, "wgrad", L["flop"],
+                      lambda: un.rbgs_conv_backward(L["x"], L["w"], L["g"], None, L["dw"], None, accumulate=True))
+                un.rbgs_conv_backward(L["x"], L["w"], L["g"], None, None, L["db"], accumulate=True)
+
+    flop = 0.0
+    for L in layers:
+        flop += L["flop"] * (("fwd" in ops) + ("dgrad" in ops and L["dx"] is not None) + ("wgrad" in ops))
+    engines = ("tcgen05", "mma_sync") if args.engine == "both" else (args.engine,)
+    results = {}
+    clocks = None
+    peaks = measured_peaks() or {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    for name in engines:
+        un.rbgs_conv_set_engine(un.RBGS_CONV_TCGEN05 if name == "tcgen05" else un.RBGS_CONV_MMA_SYNC)
+        for _ in range(args.warmup):
+            step()
+        un.rbgs_conv_check(dev)
+        torch.cuda.synchronize(dev)
+        uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+        sampler = ClockSampler(str(uuid) if uuid else None)
+        ev = []
+        with sampler:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step(ev)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        un.rbgs_conv_check(dev)
+        t = e0.elapsed_time(e1) / 1e3 / args.steps
+        per = {}
+        for key, fl, a, b in ev:
+            acc = per.setdefault(key, [0.0, 0.0])
+            acc[0] += fl
+            acc[1] += a.elapsed_time(b) / 1e3
+        results[name] = dict(tflops=flop / t / 1e12, ms_per_step=1e3 * t,
+                             products={k: {"tflops": v[0] / v[1] / 1e12, "ms_per_step": 1e3 * v[1] / args.steps}
+                                       for k, v in per.items() if v[1] > 0})
+        if name == engines[0]:
+            clocks = sampler.summary()
+    un.rbgs_conv_set_engine(un.RBGS_CONV_TCGEN05)
+    main_e = engines[0]
+    r = results[main_e]
+    # dominant product: the one taking the most time per step
+    dom = max(r["products"], key=lambda k: r["products"][k]["ms_per_step"])
+    achieved = r["products"][dom]["tflops"]
+    line = {"metric": "TFLOP/s (U-Net convolution products: forward, data and weight gradients)",
+            "value": r["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"U-Net layers {list(idx)} at batch {B}, level-0 {hw}x{hw}, ops {list(ops)}",
+                       "engine": main_e, "l2": "per step all layers' operands, larger than L2 at the default size"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"conv_umma_kernel ({dom}: the product taking the most time), "
+                                   "of measured bf16 burst peak"},
+            "engines": results, "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def _solve_from(rb, n, h2, f, u0, tol, cap, chunk):
     """Mixed-precision solve from u0 in chunks of `chunk` sweeps up to `cap`; returns
     (sweeps, rho, seconds, extrapolated sweeps to tol or None)."""
@@ -431,6 +563,8 @@ def main():
         return run_batched(args)
     if args.mode == "learned":
         return run_learned(args)
+    if args.mode == "conv":
+        return run_conv(args)
     import torch
     import torch.distributed as dist
 
