@@ -7,7 +7,8 @@
 //
 //  * quarter(s): s * 0.25 by subtracting 2 from the biased exponent whenever the result
 //    stays a normal number (biased exponent of s in 3..2046), which is exact; zeros,
-//    subnormal results, Inf and NaN take the ordinary multiply.
+//    subnormal results, Inf and NaN go through an integer rounding of the significand
+//    (quarter_bits_small), so the multiply never reaches the FP64 pipe.
 //  * add_int(a, b): IEEE 754 binary64 addition with round-to-nearest-even, written from
 //    the standard's definition (align, add or subtract the 53-bit significands with
 //    guard bits and a sticky bit, normalise, round half to even).  It handles finite
@@ -45,6 +46,25 @@ inline double hw_mul(double a, double b) { volatile double p = a * b; return p; 
 // neither evaluate it speculatively nor predicate it into the common path (either would
 // put an FP64 instruction back on the pipe for every update).  All 32 lanes of the warp
 // must call it together.
+// s * 0.25 for the cases the exponent decrement cannot take (biased exponent 0, 1, 2 or
+// 2047), from the definition of the binary64 format: Inf and NaN are returned unchanged;
+// otherwise s = m 2^(max(e, 1) - 1075) with m the significand (implicit bit included when
+// e > 0), so s / 4 = (m / 2^k) 2^-1074 with k = 1 for e = 2 and k = 2 for e = 0, 1: a
+// subnormal (or zero) whose significand is m / 2^k rounded half to even.  A carry to 2^52
+// is the encoding of the smallest normal number, so sign | q is the result in every case.
+// Integer operations only: the FP64 pipe never sees this path.
+__host__ __device__ __forceinline__ uint64_t quarter_bits_small(uint64_t u) {
+    const unsigned e = (unsigned)(u >> 52) & 0x7FFu;
+    if (e == 0x7FFu) return u;
+    const uint64_t sign = u & 0x8000000000000000ull;
+    const uint64_t m = (u & 0x000FFFFFFFFFFFFFull) | (e ? 0x0010000000000000ull : 0ull);
+    const unsigned k = e == 2u ? 1u : 2u;
+    uint64_t q = m >> k;
+    const uint64_t rem = m & ((1ull << k) - 1ull), half = 1ull << (k - 1u);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    return sign | q;
+}
+
 __host__ __device__ __forceinline__ double quarter(double s) {
 #if defined(__CUDA_ARCH__)
     const int hi = __double2hiint(s);
@@ -53,14 +73,14 @@ __host__ __device__ __forceinline__ double quarter(double s) {
     const bool fast = e - 3u <= 2043u;
     double r = __hiloint2double(hi - (2 << 20), lo);
     if (__any_sync(0xffffffffu, !fast)) {
-        if (!fast) asm volatile("mul.rn.f64 %0, %1, 0d3FD0000000000000;" : "=d"(r) : "d"(s));
+        if (!fast) r = bitsd(quarter_bits_small(dbits(s)));
     }
     return r;
 #else
     uint64_t u = dbits(s);
     unsigned e = (unsigned)(u >> 52) & 0x7FFu;
     if (e - 3u <= 2043u) return bitsd(u - (2ull << 52));
-    return hw_mul(s, 0.25);
+    return bitsd(quarter_bits_small(u));
 #endif
 }
 

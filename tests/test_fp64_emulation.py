@@ -140,7 +140,17 @@ def test_quarter(lib):
     tiny = np.finfo(np.float64).tiny
     special = np.array([0.0, -0.0, tiny, 2 * tiny, 4 * tiny, 3 * tiny, 6 * tiny, 5e-324, np.inf,
                         -np.inf, np.nan, np.finfo(np.float64).max, 1.0, -3.0])
-    a = np.concatenate([a, special])
+    # every rounding case of the integer path: biased exponents 0, 1, 2 (subnormal or zero
+    # results, ties to even, carries into the smallest normal), 3 (the first exponent-
+    # decrement case), both signs, random and extreme significands
+    low = []
+    for e in (0, 1, 2, 3):
+        mant = np.concatenate([rng.integers(0, 2 ** 52, 20000, dtype=np.uint64),
+                               np.arange(0, 16, dtype=np.uint64),
+                               np.uint64(2 ** 52) - np.arange(1, 17, dtype=np.uint64)])
+        for sgn in (0, 1):
+            low.append((np.uint64(sgn) << np.uint64(63)) | (np.uint64(e) << np.uint64(52)) | mant)
+    a = np.concatenate([a, special, _bits_to_f(np.concatenate(low))])
     out = np.empty_like(a)
     lib.check_quarter(a.size, _p(a), _p(out))
     with np.errstate(all="ignore"):
