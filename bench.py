@@ -52,8 +52,8 @@ def parse():
     p.add_argument("--values", type=int, default=0, help="values per thread in a half-sweep (0 auto, 2, 4)")
     p.add_argument("--rows", type=int, default=0, help="rows per loop step in a half-sweep (0 auto, 1, 2)")
     p.add_argument("--int-rows", type=int, default=0, help="hybrid FP64: integer-pipe rows per strip pair")
-    p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one launch per colour, 2 temporal")
-    p.add_argument("--tblock-k", type=int, default=0, help="sweeps per temporal pass (0 auto)")
+    p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one launch per colour, 2 temporal (TMA tiles), 3 register wavefront")
+    p.add_argument("--tblock-k", type=int, default=0, help="sweeps per temporal or wavefront pass (0 auto)")
     p.add_argument("--precision", choices=["fp64", "refine"], default="fp64",
                    help="fp64: plain FP64 sweeps; refine: FP32 sweeps with FP64 defect correction")
     p.add_argument("--inner", type=int, default=0, help="FP32 sweeps per correction (refine)")
@@ -120,6 +120,18 @@ def profiled_traffic(emulate):
         return float(vals["traffic_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def resolved_kernel(n, refine, kernel, tblock_k):
+    """The sweep kernel and depth the library runs (RBGS_KERNEL_AUTO as documented in
+    include/rbgs.h): 1 one launch per colour, 2 TMA tiles, 3 register wavefront."""
+    if kernel:
+        return kernel, (tblock_k or (4 if refine else 2))
+    if tblock_k:
+        return 1, 1
+    if refine:
+        return (3, 4) if n > 2048 else (1, 1)
+    return (3, 2) if 2048 < n < 8192 else (1, 1)
 
 
 def measured_peaks():
@@ -695,16 +707,16 @@ def main():
         rb.rbgs_destroy(ctx)
         return rho
 
+    kernel, kdepth = resolved_kernel(n, refine, args.kernel, args.tblock_k)
+    blocked = kernel in (2, 3)  # several sweeps per launch (TMA tiles or register wavefront)
     # pack f, pack u, ||b|| (2), the sweeps, residual (3), unpack
     if refine:
         inner = args.inner or 100
         outer = -(-sweeps // inner)
-        k32 = args.tblock_k or 4
-        per_outer = 4 + 1 + 3 + (inner // k32 + 2 * (inner % k32) if args.kernel == 2 else 2 * inner)
+        per_outer = 4 + 1 + 3 + (inner // kdepth + 2 * (inner % kdepth) if blocked else 2 * inner)
         launches_per_step = 4 + 4 + outer * per_outer + 3 + 1
-    elif args.kernel == 2:
-        k = args.tblock_k or 2
-        launches_per_step = 4 + sweeps // k + 2 * (sweeps % k) + 3 + 1
+    elif blocked:
+        launches_per_step = 4 + sweeps // kdepth + 2 * (sweeps % kdepth) + 3 + 1
     else:
         launches_per_step = 4 + 2 * sweeps + 3 + 1
 
@@ -733,24 +745,32 @@ def main():
     hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0)) if peaks else 2070.0
-    temporal = args.kernel == 2
+    names = {2: "temporal_tile", 3: "wavefront_kernel"}
     if refine:
-        # dominant kernel: the FP32 inner half-sweep (12 algorithmic bytes per update)
-        kname = "temporal_tile<float>" if temporal else "half_sweep_f32"
-        per_launch_lups = n * n / 2.0
-        launch_s = sweep_s / (2 * sweeps * args.steps)  # per half-sweep equivalent
-        alg_bytes = 12 * per_launch_lups
+        # dominant kernel: the FP32 inner sweeps (12 algorithmic bytes per update for one
+        # launch per colour; a blocked pass moves the same bytes for kdepth sweeps)
+        kname = f"{names[kernel]}<float, {kdepth}>" if blocked else "half_sweep_f32"
+        if blocked:  # one pass: kdepth sweeps of every point, the iterate and h2f moved once
+            launches = max(sweeps // kdepth, 1)
+            per_launch_lups = float(n) * n * kdepth
+            alg_bytes = 12.0 * n * n
+        else:  # one half-sweep: half the points
+            launches = 2 * sweeps
+            per_launch_lups = n * n / 2.0
+            alg_bytes = 12 * per_launch_lups
+        launch_s = sweep_s / (launches * args.steps)
         achieved = alg_bytes / launch_s / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
                     "frac": achieved / peak_hbm, "traffic": None, "kernel": kname, "peak_source": hbm_src,
                     "launch_ms": 1e3 * launch_s, "algorithmic_bytes_per_launch": alg_bytes,
-                    "note": "per half-sweep equivalent, including the FP64 defect/correction passes"}
+                    "note": "per launch equivalent (a half-sweep, or a blocked pass), including the "
+                            "FP64 defect/correction passes in the time"}
     else:
         # dominant kernel: the FP64 half-sweep, bound by the FP64 pipe: 4 correctly rounded
         # adds per update (the x0.25 runs on the integer pipe).  Peak: 2 FP64 instructions
         # per clock per SM (ncu's DFMA peak_sustained) x SMs x maximum SM clock.
-        launches = (sweeps // max(args.tblock_k or 2, 1)) if temporal else 2 * sweeps
-        kname = "temporal_tile<double>" if temporal else "half_sweep_f64"
+        launches = (sweeps // kdepth) if blocked else 2 * sweeps
+        kname = f"{names[kernel]}<double, {kdepth}>" if blocked else "half_sweep_f64"
         per_launch_lups = n * n * sweeps / launches
         launch_s = sweep_s / (launches * args.steps)
         fp64_ops = 4 * per_launch_lups
@@ -758,7 +778,7 @@ def main():
         peak_alu = 2.0 * sm_count * sm_mhz * 1e6 / 1e12
         alg_bytes = BYTES_PER_LUP * per_launch_lups
         hbm_achieved = alg_bytes / launch_s / 1e9
-        traffic = None if temporal else profiled_traffic(args.emulate)
+        traffic = None if blocked else profiled_traffic(args.emulate)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                     "frac": achieved / peak_alu, "traffic": traffic, "kernel": kname,
                     "peak_source": f"FP64 pipe: 2 instr/clk/SM x {sm_count} SMs x {sm_mhz:.0f} MHz "
@@ -801,8 +821,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 f ~ U(-1,1))",
             "config": {"workload": workload(n, sweeps, args.precision), "n": n, "sweeps": sweeps,
-                       "kernel": "one launch per colour" if args.kernel in (0, 1) else "temporal",
-                       "tblock_k": args.tblock_k or "auto", "precision": args.precision,
+                       "kernel": {1: "one launch per colour", 2: "temporal (TMA tiles)",
+                                  3: "register wavefront"}[kernel],
+                       "tblock_k": kdepth if blocked else None, "precision": args.precision,
                        "fp64_emulate": args.emulate, "tile_rows": args.tile_rows or "auto",
                        "sweep_values": args.values or "auto", "sweep_rows": args.rows or "auto",
                        "int_rows": args.int_rows,

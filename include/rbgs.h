@@ -54,9 +54,12 @@ typedef enum {
 } rbgs_precision;
 
 typedef enum {
-    RBGS_KERNEL_AUTO = 0,
+    RBGS_KERNEL_AUTO = 0,     /* with tblock_k = 0: WAVEFRONT (depth 2) for FP64 sweeps when
+                                 2048 < n < 8192 and (depth 4) for the FP32 inner sweeps when
+                                 n > 2048, COLOUR otherwise; with tblock_k set: COLOUR      */
     RBGS_KERNEL_COLOUR = 1,   /* one launch per colour (half-sweep kernels)               */
-    RBGS_KERNEL_TEMPORAL = 2  /* several sweeps per shared-memory tile, halo recompute      */
+    RBGS_KERNEL_TEMPORAL = 2, /* several sweeps per shared-memory tile, halo recompute      */
+    RBGS_KERNEL_WAVEFRONT = 3 /* several sweeps per pass, a register wavefront per strip   */
 } rbgs_kernel;
 
 typedef struct {
@@ -64,7 +67,9 @@ typedef struct {
     int kernel;        /* rbgs_kernel                                                     */
     int check_every;   /* sweeps between residual checks in rbgs_solve (0: 100)            */
     long max_sweeps;   /* rbgs_solve gives up after this many sweeps (0: 1e9)              */
-    int tblock_k;      /* sweeps per tile pass for RBGS_KERNEL_TEMPORAL (0: automatic)     */
+    int tblock_k;      /* sweeps per pass: RBGS_KERNEL_TEMPORAL 1, 2, 4 (FP64) or 2, 4, 8
+                          (FP32 inner sweeps); RBGS_KERNEL_WAVEFRONT 2, 4 (FP64) or 2, 4, 6
+                          (FP32 inner sweeps); 0: automatic                                */
     int tile_rows;     /* rows per thread block (0: automatic)                             */
     int fp64_emulate;  /* FP64 adds issued on the integer pipe per 8 (-1: automatic)       */
     int inner_sweeps;  /* FP32 sweeps per defect correction for RBGS_FP32_REFINE (0: auto) */

@@ -133,7 +133,7 @@ rbgs_status ensure_f32(rbgs_ctx *c) {
         rbgs_status st;
         if ((st = alloc_zero(reinterpret_cast<void **>(&c->f32.u[q]), bytes, c->stream)) != RBGS_OK) return st;
         if ((st = alloc_zero(reinterpret_cast<void **>(&c->f32.hf[q]), bytes, c->stream)) != RBGS_OK) return st;
-        if (c->kernel32 == RBGS_KERNEL_TEMPORAL &&
+        if ((c->kernel32 == RBGS_KERNEL_TEMPORAL || c->kernel32 == RBGS_KERNEL_WAVEFRONT) &&
             (st = alloc_zero(reinterpret_cast<void **>(&c->f32.alt[q]), bytes, c->stream)) != RBGS_OK)
             return st;
     }
@@ -154,6 +154,14 @@ rbgs_status check_device_status(rbgs_ctx *c) {
 
 rbgs_status enqueue_sweeps(rbgs_ctx *c, long nsweeps, cudaStream_t s) {
     if (c->kernel == RBGS_KERNEL_TEMPORAL) return launch_temporal_sweeps(c, nsweeps, s);
+    if (c->kernel == RBGS_KERNEL_WAVEFRONT) {
+        const long passes = nsweeps / c->tblock_k;
+        for (long q = 0; q < passes; ++q) {
+            rbgs_status st = launch_wavefront_pass<double>(c->f64, c->tblock_k, s);
+            if (st != RBGS_OK) return st;
+        }
+        nsweeps -= passes * c->tblock_k;
+    }
     return launch_sweeps_f64(c, nsweeps, s);
 }
 
@@ -225,11 +233,13 @@ rbgs_status inner_sweeps_f32(rbgs_ctx *c, long m) {
         RBGS_CUDA(cudaGraphLaunch(c->graph32, c->stream));
         return RBGS_OK;
     }
-    if (c->kernel32 == RBGS_KERNEL_TEMPORAL) {
+    if (c->kernel32 == RBGS_KERNEL_TEMPORAL || c->kernel32 == RBGS_KERNEL_WAVEFRONT) {
         const int k = c->tblock_k32;
         const long passes = m / k;
         for (long q = 0; q < passes; ++q) {
-            rbgs_status st = launch_temporal_pass<float>(c->f32, k, c->dstatus, c->stream);
+            rbgs_status st = c->kernel32 == RBGS_KERNEL_TEMPORAL
+                                 ? launch_temporal_pass<float>(c->f32, k, c->dstatus, c->stream)
+                                 : launch_wavefront_pass<float>(c->f32, k, c->stream);
             if (st != RBGS_OK) return st;
         }
         m -= passes * k;
@@ -308,7 +318,7 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     if (o.precision != RBGS_FP64 && o.precision != RBGS_FP32_REFINE) {
         set_error("unknown precision %d", o.precision); return RBGS_EINVAL;
     }
-    if (o.kernel < RBGS_KERNEL_AUTO || o.kernel > RBGS_KERNEL_TEMPORAL) {
+    if (o.kernel < RBGS_KERNEL_AUTO || o.kernel > RBGS_KERNEL_WAVEFRONT) {
         set_error("unknown kernel %d", o.kernel); return RBGS_EINVAL;
     }
     if (o.fp64_emulate != -1 && !emulation_split_supported(o.fp64_emulate)) {
@@ -326,11 +336,22 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     if (o.tile_rows < 0 || o.tblock_k < 0 || o.inner_sweeps < 0) {
         set_error("negative tile_rows / tblock_k / inner_sweeps"); return RBGS_EINVAL;
     }
-    if (o.tblock_k && o.precision == RBGS_FP64 && o.tblock_k != 1 && o.tblock_k != 2 && o.tblock_k != 4) {
-        set_error("tblock_k for FP64 sweeps must be 1, 2 or 4"); return RBGS_EINVAL;
-    }
-    if (o.tblock_k && o.precision == RBGS_FP32_REFINE && o.tblock_k != 2 && o.tblock_k != 4 && o.tblock_k != 8) {
-        set_error("tblock_k for FP32 inner sweeps must be 2, 4 or 8"); return RBGS_EINVAL;
+    if (o.kernel == RBGS_KERNEL_WAVEFRONT) {
+        if (o.tblock_k && o.precision == RBGS_FP64 && o.tblock_k != 2 && o.tblock_k != 4) {
+            set_error("tblock_k of the FP64 wavefront must be 2 or 4"); return RBGS_EINVAL;
+        }
+        if (o.tblock_k && o.precision == RBGS_FP32_REFINE && o.tblock_k != 2 && o.tblock_k != 4 &&
+            o.tblock_k != 6) {
+            set_error("tblock_k of the FP32 wavefront must be 2, 4 or 6"); return RBGS_EINVAL;
+        }
+    } else {
+        if (o.tblock_k && o.precision == RBGS_FP64 && o.tblock_k != 1 && o.tblock_k != 2 && o.tblock_k != 4) {
+            set_error("tblock_k for FP64 sweeps must be 1, 2 or 4"); return RBGS_EINVAL;
+        }
+        if (o.tblock_k && o.precision == RBGS_FP32_REFINE && o.tblock_k != 2 && o.tblock_k != 4 &&
+            o.tblock_k != 8) {
+            set_error("tblock_k for FP32 inner sweeps must be 2, 4 or 8"); return RBGS_EINVAL;
+        }
     }
 
     rbgs_ctx *c = new (std::nothrow) rbgs_ctx();
@@ -339,7 +360,14 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     c->h2 = h2;
     c->opts = o;
     c->stream = (cudaStream_t)cuda_stream;
-    c->kernel = o.kernel == RBGS_KERNEL_AUTO ? RBGS_KERNEL_COLOUR : o.kernel;
+    // automatic kernels (measured on GB300): the register wavefront for FP64 sweeps on
+    // mid-size grids, where it beats one launch per colour (at 4095^2 by ~20%; from 8191^2
+    // up both run at the FP64-pipe limit), and for the FP32 inner sweeps above 2048^2
+    // (1.5-1.6x); one launch per colour (with graphs) on smaller grids
+    const bool auto_k = o.kernel == RBGS_KERNEL_AUTO && o.tblock_k == 0;
+    c->kernel = o.kernel == RBGS_KERNEL_AUTO ? ((auto_k && n > 2048 && n < 8192) ? RBGS_KERNEL_WAVEFRONT
+                                                                                 : RBGS_KERNEL_COLOUR)
+                                             : o.kernel;
     c->emulate = o.fp64_emulate == -1 ? 0x00 : o.fp64_emulate;
     c->pts = o.sweep_values ? o.sweep_values : 2;
     if (o.tile_rows) {
@@ -361,9 +389,11 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     c->int_rows = o.int_rows > 0 ? o.int_rows : 0;
     // FP64 sweeps: temporal depth (used when kernel == TEMPORAL)
     c->tblock_k = (o.precision == RBGS_FP64 && o.tblock_k) ? o.tblock_k : 2;
-    // FP32 inner sweeps of the refinement: one launch per colour unless told otherwise (the
-    // temporally blocked tiles measured slower on GB300)
-    c->kernel32 = o.kernel == RBGS_KERNEL_AUTO ? RBGS_KERNEL_COLOUR : o.kernel;
+    // FP32 inner sweeps of the refinement (the TMA-tiled temporal kernel measured slower
+    // than one launch per colour on GB300; the register wavefront faster above 2048^2)
+    c->kernel32 = o.kernel == RBGS_KERNEL_AUTO ? ((auto_k && n > 2048) ? RBGS_KERNEL_WAVEFRONT
+                                                                       : RBGS_KERNEL_COLOUR)
+                                               : o.kernel;
     c->tblock_k32 = (o.precision == RBGS_FP32_REFINE && o.tblock_k) ? o.tblock_k : 4;
     c->inner_sweeps = o.inner_sweeps ? o.inner_sweeps : 100;
     c->f64.n = n;
@@ -398,7 +428,7 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
         return RBGS_ECUDA;
     }
     rbgs_status st = RBGS_OK;
-    if (c->kernel == RBGS_KERNEL_TEMPORAL) st = ensure_f64_alt(c);
+    if (c->kernel == RBGS_KERNEL_TEMPORAL || c->kernel == RBGS_KERNEL_WAVEFRONT) st = ensure_f64_alt(c);
     if (st == RBGS_OK) st = load_problem(c, f, u_init);
     if (st != RBGS_OK) {
         free_ctx(c);

@@ -123,6 +123,9 @@ rbgs_status launch_temporal_sweeps(rbgs_ctx *c, long nsweeps, cudaStream_t s);
 template <typename T>
 rbgs_status launch_temporal_pass(ColourField<T> &fld, int k, int *status, cudaStream_t s);
 rbgs_status launch_sweeps_f32(const ColourField<float> &fld, long nsweeps, cudaStream_t s);
+// one register-wavefront pass of k sweeps from fld.u into fld.alt, then swaps them (wavefront.cu)
+template <typename T>
+rbgs_status launch_wavefront_pass(ColourField<T> &fld, int k, cudaStream_t s);
 // mixed-precision refinement kernels (mixed.cu)
 rbgs_status launch_defect(const rbgs_ctx *c, bool write_r32, double scale, cudaStream_t s);  // -> dsum[0] sum, dsum[2] max
 rbgs_status launch_correct(const rbgs_ctx *c, double scale, cudaStream_t s);
