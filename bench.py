@@ -131,7 +131,7 @@ def resolved_kernel(n, refine, kernel, tblock_k):
         return 1, 1
     if refine:
         return (3, 4) if n > 2048 else (1, 1)
-    return (3, 2) if 2048 < n < 8192 else (1, 1)
+    return 1, 1
 
 
 def measured_peaks():

@@ -54,9 +54,8 @@ typedef enum {
 } rbgs_precision;
 
 typedef enum {
-    RBGS_KERNEL_AUTO = 0,     /* with tblock_k = 0: WAVEFRONT (depth 2) for FP64 sweeps when
-                                 2048 < n < 8192 and (depth 4) for the FP32 inner sweeps when
-                                 n > 2048, COLOUR otherwise; with tblock_k set: COLOUR      */
+    RBGS_KERNEL_AUTO = 0,     /* COLOUR, except WAVEFRONT (depth 4) for the FP32 inner
+                                 sweeps of RBGS_FP32_REFINE when n > 2048 and tblock_k = 0 */
     RBGS_KERNEL_COLOUR = 1,   /* one launch per colour (half-sweep kernels)               */
     RBGS_KERNEL_TEMPORAL = 2, /* several sweeps per shared-memory tile, halo recompute      */
     RBGS_KERNEL_WAVEFRONT = 3 /* several sweeps per pass, a register wavefront per strip   */

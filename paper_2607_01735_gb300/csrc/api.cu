@@ -360,14 +360,12 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     c->h2 = h2;
     c->opts = o;
     c->stream = (cudaStream_t)cuda_stream;
-    // automatic kernels (measured on GB300): the register wavefront for FP64 sweeps on
-    // mid-size grids, where it beats one launch per colour (at 4095^2 by ~20%; from 8191^2
-    // up both run at the FP64-pipe limit), and for the FP32 inner sweeps above 2048^2
-    // (1.5-1.6x); one launch per colour (with graphs) on smaller grids
+    // automatic kernels (measured on GB300): FP64 sweeps run one launch per colour (the
+    // register wavefront reaches the same FP64-pipe limit, with overlap work on top); the
+    // FP32 inner sweeps of the refinement run the register wavefront above 2048^2 (1.6x)
+    // and one launch per colour (with graphs) on smaller grids
     const bool auto_k = o.kernel == RBGS_KERNEL_AUTO && o.tblock_k == 0;
-    c->kernel = o.kernel == RBGS_KERNEL_AUTO ? ((auto_k && n > 2048 && n < 8192) ? RBGS_KERNEL_WAVEFRONT
-                                                                                 : RBGS_KERNEL_COLOUR)
-                                             : o.kernel;
+    c->kernel = o.kernel == RBGS_KERNEL_AUTO ? RBGS_KERNEL_COLOUR : o.kernel;
     c->emulate = o.fp64_emulate == -1 ? 0x00 : o.fp64_emulate;
     c->pts = o.sweep_values ? o.sweep_values : 2;
     if (o.tile_rows) {

@@ -24,6 +24,8 @@
 // correctly rounded, so a pass equals K one-launch-per-colour sweeps bit for bit.
 // Traffic per pass: the iterate read and written once and h2f read once (plus the
 // overlaps): 12 bytes per point per K sweeps in FP32, 24 in FP64.
+#include <type_traits>
+
 #include "common.cuh"
 #include "fp64.cuh"
 #include "sweep_impl.cuh"
@@ -141,19 +143,30 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
         prefetch2(a.hf0, a.hf1, t_s + 2 + d);
     }
 
-    for (int base = t_s; base <= t_e; base += WS) {
+    // Blocks of WS steps whose rows, loads and stores all lie inside the grid and the
+    // segment, on a strip with no boundary column, run without any of those checks.
+    const bool full_cols = __all_sync(0xffffffffu, msk0 == (1u << P) - 1 && msk1 == (1u << P) - 1);
+    auto run_block = [&](int base, auto fast_tag) {
+        constexpr bool FAST = decltype(fast_tag)::value;
 #pragma unroll
         for (int u = 0; u < WS; ++u) {
             const int t = base + u;  // t - t_s = u (mod WS), and t has the parity of u
-            if (t <= t_e) {
+            if (FAST || t <= t_e) {
                 prefetch2(a.u0, a.u1, t + 3 + kWfPrefetch);
                 prefetch2(a.hf0, a.hf1, t + 2 + kWfPrefetch);
-                load2(uw[(u + WS - 1) % WS], a.u0, a.u1, t + 3);
-                load2(fw[(u + WS - 2) % WS], a.hf0, a.hf1, t + 2);
+                if (FAST) {
+                    wf_load(uw[(u + WS - 1) % WS][0], a.u0 + (size_t)(t + 3) * W + k0);
+                    wf_load(uw[(u + WS - 1) % WS][1], a.u1 + (size_t)(t + 3) * W + k0);
+                    wf_load(fw[(u + WS - 2) % WS][0], a.hf0 + (size_t)(t + 2) * W + k0);
+                    wf_load(fw[(u + WS - 2) % WS][1], a.hf1 + (size_t)(t + 2) * W + k0);
+                } else {
+                    load2(uw[(u + WS - 1) % WS], a.u0, a.u1, t + 3);
+                    load2(fw[(u + WS - 2) % WS], a.hf0, a.hf1, t + 2);
+                }
 #pragma unroll
                 for (int h = 1; h <= 2 * K; ++h) {
                     const int i = t - h + 1;
-                    if (i >= 1 && i <= n) {
+                    if (FAST || (i >= 1 && i <= n)) {
                         const int c = (h - 1) & 1;          // colour updated by half-sweep h
                         const int p = (u - h + 1 + c) & 1;  // (i + c) & 1
                         const int sm = (u - 3 - h + 2 * WS) % WS;  // slot of row i
@@ -169,20 +182,20 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
 #pragma unroll
                             for (int q = 0; q < P; ++q) {
                                 const T r = wf_update(f[q], up[q], dn[q], q ? mid[q - 1] : prev, mid[q], a.one);
-                                if ((msk >> q) & 1u) self[q] = r;
+                                if (FAST || ((msk >> q) & 1u)) self[q] = r;
                             }
                         } else {  // at k, k+1
                             const T next = __shfl_down_sync(0xffffffffu, mid[0], 1);
 #pragma unroll
                             for (int q = 0; q < P; ++q) {
                                 const T r = wf_update(f[q], up[q], dn[q], mid[q], q + 1 < P ? mid[q + 1] : next, a.one);
-                                if ((msk >> q) & 1u) self[q] = r;
+                                if (FAST || ((msk >> q) & 1u)) self[q] = r;
                             }
                         }
                     }
                 }
                 const int r = t - 2 * K + 1;  // final: every half-sweep has passed it
-                if (r >= row_a && r < row_b && kin) {
+                if ((FAST || (r >= row_a && r < row_b)) && kin) {
                     const T(&v)[2][P] = uw[(u + 1) % WS];
                     T *d0 = a.o0 + (size_t)r * W + k0, *d1 = a.o1 + (size_t)r * W + k0;
                     if (k0 >= olo && k0 + P <= ohi) {
@@ -200,6 +213,14 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
                 }
             }
         }
+    };
+    for (int base = t_s; base <= t_e; base += WS) {
+        const bool fast = full_cols && base >= 2 * K && base + WS + 2 <= n + 1 && base + WS - 1 <= t_e &&
+                          base - 2 * K + 1 >= row_a && base + WS - 2 * K < row_b;
+        if (fast)
+            run_block(base, std::true_type{});
+        else
+            run_block(base, std::false_type{});
     }
 }
 

@@ -135,3 +135,32 @@ def test_wavefront_refinement_reaches_tolerance_like_oracle():
         s.get_solution(out)
     assert st == rb.RBGS_OK and done == done_ref
     _assert_bits(out.cpu().numpy(), ref)
+
+
+def test_full_size_kernels_agree_bitwise():
+    """16384^2 (the benchmark grid): the wavefront and one launch per colour give the same
+    bits, for FP64 sweeps and for the refinement's FP32 inner sweeps.  Both are pinned to
+    the oracle at smaller sizes; equality is what carries that pin to the full size."""
+    n = 16384
+    h2 = synth.h_squared(n)
+    f = synth.uniform_pm1_grid(n, 1, device="cuda")
+    u0 = torch.zeros(n + 2, n + 2, dtype=torch.float64, device="cuda")
+    outs = []
+    for kernel, k in ((rb.RBGS_KERNEL_COLOUR, 0), (rb.RBGS_KERNEL_WAVEFRONT, 2)):
+        out = torch.empty_like(u0)
+        with rb.Solver(n, h2, f, u0, kernel=kernel, tblock_k=k) as s:
+            s.sweep(5)
+            s.get_solution(out)
+        outs.append(out)
+    assert torch.equal(outs[0].view(torch.int64), outs[1].view(torch.int64))
+    del outs
+    outs = []
+    for kernel, k in ((rb.RBGS_KERNEL_COLOUR, 0), (rb.RBGS_KERNEL_WAVEFRONT, 4)):
+        out = torch.empty_like(u0)
+        with rb.Solver(n, h2, f, u0, precision=rb.RBGS_FP32_REFINE, kernel=kernel, tblock_k=k,
+                       inner_sweeps=10, max_sweeps=20) as s:
+            done, rho, st = s.solve(1e-30, allow_not_converged=True)
+            s.get_solution(out)
+        assert done == 20
+        outs.append(out)
+    assert torch.equal(outs[0].view(torch.int64), outs[1].view(torch.int64))
