@@ -794,12 +794,13 @@ def main():
         oh = torch.empty(n + 2, n + 2, dtype=torch.float64).pin_memory()
         step(fh, uh, oh)  # warm the host path once
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step(fh, uh, oh)
-        e1.record(stream)
-        barrier()
+        with ClockSampler(str(uuid) if uuid else None) as e2e_clocks:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step(fh, uh, oh)
+            e1.record(stream)
+            barrier()
         et = e0.elapsed_time(e1) / 1e3
         if world > 1:
             tt = torch.tensor([et], dtype=torch.float64, device=dev)
@@ -808,7 +809,7 @@ def main():
         e2e = {"value": lups / et / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 8 * (n * n + (n + 2) * (n + 2)),
                "d2h_bytes_per_step": 8 * (n + 2) * (n + 2) + 8,
-               "ms_per_step": 1e3 * et / args.steps}
+               "ms_per_step": 1e3 * et / args.steps, "clocks": e2e_clocks.summary()}
 
     if rank == 0:
         cpu = None
