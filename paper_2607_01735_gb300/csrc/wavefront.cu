@@ -6,10 +6,11 @@
 // h-1 of rows i-1, i, i+1.  So at step t a warp applies half-sweep h to row t-h+1 for
 // h = 1, 2, ..., 2K in that order: half-sweep h-1 has just reached row t-h+2, and
 // half-sweep h+1 has not yet touched row t-h.  Row t-2K+1 is then final and is stored.
-// The live rows of the iterate (t-2K .. t+3, loaded three steps ahead) and of h2f
-// (t-2K+1 .. t+2) sit in rings of 2K+4 register slots; the step loop is unrolled over
-// the ring so every slot index is a compile-time constant.  Rows further ahead are
-// prefetched into L1.
+// The live rows of the iterate (t-2K .. t+3, loaded three steps ahead) sit in a ring of
+// 2K+4 register slots; the step loop is unrolled over the ring so every slot index is a
+// compile-time constant.  The live rows of h2f (t-2K+1 .. t+2) sit in a ring of the same
+// slots in shared memory, filled by cp.async two steps ahead (which frees the registers
+// for more resident warps).  Rows of the iterate further ahead are prefetched into L1.
 //
 // Decomposition.  A warp owns a strip of 64 values of each colour row (2 per lane) and a
 // segment of rows.  The west/east neighbour across lanes comes by shuffle; at the strip's
@@ -72,6 +73,16 @@ __device__ __forceinline__ void wf_load(double *v, const double *p) {
     v[0] = t.x, v[1] = t.y;
 }
 
+__device__ __forceinline__ void wf_load_shared(float *v, const float *p) {
+    const float2 t = *reinterpret_cast<const float2 *>(p);
+    v[0] = t.x, v[1] = t.y;
+}
+
+__device__ __forceinline__ void wf_load_shared(double *v, const double *p) {
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    v[0] = t.x, v[1] = t.y;
+}
+
 __device__ __forceinline__ void wf_store(float *p, const float *v) {
     *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
 }
@@ -80,11 +91,28 @@ __device__ __forceinline__ void wf_store(double *p, const double *v) {
     *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
 }
 
+// cp.async of the lane's 2 values (8 or 16 bytes) into shared memory; src_valid = false
+// fills zeros without reading
+template <typename T>
+__device__ __forceinline__ void wf_cp_async(T *dst, const T *src, bool src_valid) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_valid ? 8 : 0)
+                     : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_valid ? 16 : 0)
+                     : "memory");
+}
+
+__device__ __forceinline__ void wf_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void wf_cp_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
+
 __device__ __forceinline__ void wf_prefetch(const void *p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// Ring of WS = 2K + 4 row slots, for the iterate and for h2f alike.  With t_s the first
+// Ring of WS = 2K + 4 row slots, for the iterate (registers) and h2f (shared memory) alike.  With t_s the first
 // step and rho(i) = i - t_s + 2K, row i lives in slot rho(i) mod WS.  At step t (t - t_s =
 // u mod WS): the iterate's row t+3 is loaded into slot u-1, h2f's row t+2 into slot u-2,
 // half-sweep h works on row t-h+1 in slot u-3-h (its neighbours in the slots on either
@@ -116,7 +144,17 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
     const int t_s = row_a - 2 * K;  // even: row parities below are compile-time constants
     const int t_e = min(row_b + 2 * K - 2, n + 2 * K);
 
-    T uw[WS][2][P], fw[WS][2][P];
+    // the iterate's ring in registers; h2f's ring in shared memory, filled by cp.async and
+    // read back by the lane that copied it (no barrier: each lane reads its own bytes)
+    T uw[WS][2][P];
+    __shared__ __align__(16) T fsm[kWfWarps][WS][2][32 * P];
+    T(*fw)[2][32 * P] = fsm[threadIdx.x >> 5];
+    auto load_f = [&](int slot, int r) {
+        const bool ok = kin && r >= 0 && r <= n + 1;
+        const size_t off = ok ? (size_t)r * W + k0 : 0;
+        wf_cp_async(&fw[slot][0][lane * P], a.hf0 + off, ok);
+        wf_cp_async(&fw[slot][1][lane * P], a.hf1 + off, ok);
+    };
     auto load2 = [&](T (&dst)[2][P], const T *p0, const T *p1, int r) {
         if (kin && r >= 0 && r <= n + 1) {
             wf_load(dst[0], p0 + (size_t)r * W + k0);
@@ -136,11 +174,13 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
 #pragma unroll
     for (int r = 0; r <= 2 * K + 2; ++r) load2(uw[r], a.u0, a.u1, t_s - 2 * K + r);
 #pragma unroll
-    for (int r = 1; r <= 2 * K + 1; ++r) load2(fw[r], a.hf0, a.hf1, t_s - 2 * K + r);
+    for (int r = 1; r <= 2 * K + 1; ++r) load_f(r, t_s - 2 * K + r);
+    wf_cp_commit();
+    wf_cp_commit();  // two empty groups: the first step's wait then covers the rows above
+    wf_cp_commit();
 #pragma unroll
     for (int d = 0; d < kWfPrefetch; ++d) {
         prefetch2(a.u0, a.u1, t_s + 3 + d);
-        prefetch2(a.hf0, a.hf1, t_s + 2 + d);
     }
 
     // Blocks of WS steps whose rows, loads and stores all lie inside the grid and the
@@ -153,16 +193,15 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
             const int t = base + u;  // t - t_s = u (mod WS), and t has the parity of u
             if (FAST || t <= t_e) {
                 prefetch2(a.u0, a.u1, t + 3 + kWfPrefetch);
-                prefetch2(a.hf0, a.hf1, t + 2 + kWfPrefetch);
                 if (FAST) {
                     wf_load(uw[(u + WS - 1) % WS][0], a.u0 + (size_t)(t + 3) * W + k0);
                     wf_load(uw[(u + WS - 1) % WS][1], a.u1 + (size_t)(t + 3) * W + k0);
-                    wf_load(fw[(u + WS - 2) % WS][0], a.hf0 + (size_t)(t + 2) * W + k0);
-                    wf_load(fw[(u + WS - 2) % WS][1], a.hf1 + (size_t)(t + 2) * W + k0);
                 } else {
                     load2(uw[(u + WS - 1) % WS], a.u0, a.u1, t + 3);
-                    load2(fw[(u + WS - 2) % WS], a.hf0, a.hf1, t + 2);
                 }
+                load_f((u + WS - 2) % WS, t + 2);
+                wf_cp_commit();
+                wf_cp_wait2();  // h2f rows up to t (issued two steps ago) have landed
 #pragma unroll
                 for (int h = 1; h <= 2 * K; ++h) {
                     const int i = t - h + 1;
@@ -171,7 +210,8 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
                         const int p = (u - h + 1 + c) & 1;  // (i + c) & 1
                         const int sm = (u - 3 - h + 2 * WS) % WS;  // slot of row i
                         const int su = (sm + WS - 1) % WS, sd = (sm + 1) % WS;
-                        const T *f = fw[sm][c];
+                        T f[P];
+                        wf_load_shared(f, &fw[sm][c][lane * P]);
                         const T *mid = uw[sm][1 - c];
                         const T *up = uw[su][1 - c];
                         const T *dn = uw[sd][1 - c];
