@@ -254,6 +254,36 @@ def time_to_residual(n, tol=1e-8, stream=0):
     return out
 
 
+def small_grid_history(stream=0):
+    """The small configuration: 255^2 interior (h = 1/256), zero ring, u0 = 0, 1000 FP64
+    sweeps with the residual every 100, for f = 2 pi^2 sin(pi x) sin(pi y) and for f ~ U(-1,1);
+    wall time of the whole loop (sweeps and residuals, one context per right-hand side)."""
+    import torch
+
+    import paper_2607_01735_gb300 as rb
+    import synth
+    n = 255
+    h2 = synth.h_squared(n)
+    out = {"n": n, "sweeps": 1000, "check_every": 100}
+    for name, f in (("manufactured", torch.from_numpy(synth.manufactured_rhs(n)).cuda()),
+                    ("uniform", synth.uniform_pm1_grid(n, stream, device="cuda"))):
+        u0 = torch.from_numpy(synth.ring_grid(n)).cuda()
+        with rb.Solver(n, h2, f, u0) as s:  # warm the graph and the kernels
+            s.sweep(100)
+            s.residual()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with rb.Solver(n, h2, f, u0) as s:
+            hist = []
+            for _ in range(10):
+                s.sweep(100)
+                hist.append(s.residual())
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": dt, "us_per_sweep": 1e6 * dt / 1000, "rho_every_100": hist}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -816,6 +846,7 @@ def main():
         if not args.no_cpu_baseline:
             cpu = cpu_oracle_rate(n)
         ttr = None if args.no_ttr else time_to_residual(args.ttr_n)
+        small = None if args.no_ttr else small_grid_history()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -838,6 +869,7 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks.summary(),
             "time_to_residual": ttr,
+            "small_grid": small,
         }
         print(json.dumps(line))
     if world > 1:
