@@ -219,17 +219,40 @@ __global__ void transpose_weights_kernel(const uint16_t *__restrict__ Wt, uint16
     }
 }
 
-// db[o] += sum over pixels of G[p][o]
-__global__ void bias_grad_kernel(const uint16_t *__restrict__ G, float *__restrict__ db, long P, int Cout) {
-    const int o = blockIdx.y * 32 + (threadIdx.x & 31);
-    if (o >= Cout) return;
-    float s = 0.f;
-    for (long p = (long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); p < P;
-         p += (long)gridDim.x * (blockDim.x / 32)) {
-        __nv_bfloat16 v = reinterpret_cast<const __nv_bfloat16 *>(G)[p * Cout + o];
-        s += __bfloat162float(v);
+// db[o] += sum over pixels of G[p][o].  A thread owns 8 channels (one 16-byte vector) of
+// a pixel lane and strides over pixels; the lanes of a block are then summed in a fixed
+// order in shared memory and added to db once per block.
+constexpr int kBiasThreads = 256;
+
+__global__ void __launch_bounds__(kBiasThreads) bias_grad_kernel(const uint16_t *__restrict__ G,
+                                                                 float *__restrict__ db, long P, int Cout) {
+    __shared__ float part[kBiasThreads][8];
+    const int groups = Cout >> 3;  // 1..32
+    const int lanes = kBiasThreads / groups;
+    const int g = threadIdx.x % groups, r = threadIdx.x / groups;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r < lanes) {
+        for (long p = (long)blockIdx.x * lanes + r; p < P; p += (long)gridDim.x * lanes) {
+            const uint4 v = ld16(G + p * Cout + g * 8);
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                acc[2 * e] += __uint_as_float(w[e] << 16);
+                acc[2 * e + 1] += __uint_as_float(w[e] & 0xFFFF0000u);
+            }
+        }
     }
-    atomicAdd(db + o, s);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) part[threadIdx.x][e] = acc[e];
+    __syncthreads();
+    if (r == 0) {
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < lanes; ++q)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[e] += part[q * groups + g][e];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) atomicAdd(db + g * 8 + e, s[e]);
+    }
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -288,8 +311,7 @@ rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t 
         RBGS_LAUNCH_CHECK();
     }
     if (db) {
-        dim3 grid(256, (unsigned)((Cout + 31) / 32));
-        bias_grad_kernel<<<grid, 256, 0, s>>>(G, db, P, Cout);
+        bias_grad_kernel<<<8 * 152, kBiasThreads, 0, s>>>(G, db, P, Cout);
         RBGS_LAUNCH_CHECK();
     }
     return RBGS_OK;
@@ -297,7 +319,7 @@ rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t 
 
 bool conv_shapes_ok(int B, int H, int W, int Cin, int Cout, int ks) {
     return B >= 1 && H >= 1 && W >= 1 && Cin >= 8 && Cout >= 8 && Cin % 8 == 0 && Cout % 8 == 0 &&
-           (ks == 1 || ks == 3) && H <= 32767 && W <= 32767 && (long)B * H * W < (1L << 40);
+           Cout <= 256 * 8 && (ks == 1 || ks == 3) && H <= 32767 && W <= 32767 && (long)B * H * W < (1L << 40);
 }
 
 }  // namespace rbgs

@@ -330,6 +330,15 @@ __device__ void produce(const UArgs &a, uint32_t sbase, uint32_t stage_bytes, ui
                 dx = t % a.ks - pad;
             }
             const long shift = ((long)dy * a.W + dx) * a.Cin + c;
+            // image coordinates of the thread's 4 pixels, advanced by UK pixels per stage
+            int py[4], px[4];
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                const uint32_t p = (uint32_t)(T.kbeg + (j0 + 2 * it) * 8 + kr);
+                const uint32_t r = p - fdiv(p, a.div_hw) * HW;
+                py[it] = (int)fdiv(r, a.div_w);
+                px[it] = (int)r - py[it] * a.W;
+            }
             for (int kt = 0; kt < T.KT; ++kt) {
                 if (!wait_or_abort(&empty_bar[s], ph ^ 1u, abort_flag)) {
                     live = false;
@@ -340,15 +349,15 @@ __device__ void produce(const UArgs &a, uint32_t sbase, uint32_t stage_bytes, ui
 #pragma unroll
                 for (int it = 0; it < 4; ++it) {
                     const int p = k0 + (j0 + 2 * it) * 8 + kr;
-                    bool ok = mval && p < T.kend;
-                    if (ok) {
-                        const uint32_t r = (uint32_t)p - fdiv((uint32_t)p, a.div_hw) * HW;
-                        const int y = (int)fdiv(r, a.div_w);
-                        const int x = (int)r - y * a.W;
-                        ok = y + dy >= 0 && y + dy < a.H && x + dx >= 0 && x + dx < a.W;
-                    }
+                    const int y = py[it] + dy, x = px[it] + dx;
+                    const bool ok = mval && p < T.kend && y >= 0 && y < a.H && x >= 0 && x < a.W;
                     cp_async16(sa + (uint32_t)(j0 + 2 * it) * 2048u + a_sw,
                                ok ? a.X + (long)p * a.Cin + shift : a.X, ok);
+                    px[it] += UK;  // the same pixel lane of the next stage
+                    while (px[it] >= a.W) {
+                        px[it] -= a.W;
+                        if (++py[it] == a.H) py[it] = 0;
+                    }
                 }
 #pragma unroll
                 for (int it = 0; it < kMaxBn * 8 / kProducers; ++it) {
