@@ -79,8 +79,115 @@ __device__ __forceinline__ double bcast_max(double v, double *smem) {
 
 __device__ __forceinline__ int kact_of(int n) { return (((n + 3) / 2) + 1) & ~1; }
 
-// One FP64 half-sweep of colour C over the whole problem by this block.  The loop trip
-// count is uniform over the block (quarter() votes across the warp).
+// FP32 half-sweep of colour C over the whole problem by this block, as a row-band walk:
+// work item (column group g, band b) is a strip of V values (16 bytes) of the colour rows
+// walked down the band's rows with the other colour's rows i-1, i, i+1 in registers, so
+// each row of the other colour is loaded once per item (plus the band edges) and h2f once.
+// The west/east value that lies outside the item is read directly.  Loads are ordinary
+// (coherent) loads: the other colour was written by this block one half-sweep earlier.
+// Every thread of the block runs the same number of row steps, on rows of the same parity
+// (the FP64 quarter votes across the warp); steps past an item's band, and threads without
+// an item, compute on a valid row and store nothing.
+template <typename T>
+struct BandVec;
+template <>
+struct BandVec<float> {
+    static constexpr int V = 4;
+    __device__ static void load(float *v, const float *p) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    }
+    __device__ static void store(float *p, const float *v) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __device__ static float update(float hf, float vn, float vs, float vw, float ve) {
+        float s = __fadd_rn(hf, vn);
+        s = __fadd_rn(s, vs);
+        s = __fadd_rn(s, vw);
+        s = __fadd_rn(s, ve);
+        return __fmul_rn(s, 0.25f);
+    }
+};
+template <typename T, int C, int THREADS>
+__device__ void block_half_sweep_band(T *__restrict__ self, const T *other, const T *__restrict__ hf, int n,
+                                      int W) {
+    using BV = BandVec<T>;
+    constexpr int V = BV::V;
+    const int kact = kact_of(n);
+    const int ncol = (kact + V - 1) / V;
+    const int bands = ncol < THREADS ? THREADS / ncol : 1;
+    // rows per band, even: every band starts on an odd row, so at each step all bands sit
+    // on rows of one parity and the colour-offset branch (and the FP64 quarter's warp vote
+    // inside it) stays uniform across a warp that spans two bands
+    const int rb = ((n + bands - 1) / bands + 1) & ~1;
+    const int passes = (ncol * bands + THREADS - 1) / THREADS;  // > 1 only when ncol > THREADS
+    for (int pass = 0; pass < passes; ++pass) {
+        const int item = pass * THREADS + threadIdx.x;
+        const bool has = item < ncol * bands;
+        const int g = has ? item % ncol : 0, b = has ? item / ncol : 0;
+        const int k0 = V * g;
+        const int i0 = 1 + b * rb, i1 = min(n, i0 + rb - 1);
+        // rows i-1, i, i+1 of the other colour and h2f of row i, plus the next step's row
+        // i+2 / h2f i+1 / edge values loaded one step ahead (their latency overlaps a step)
+        T up[V], mid[V], dn[V], f[V], dn2[V], f2[V];
+        BV::load(up, other + (size_t)min(i0 - 1, n) * W + k0);
+        BV::load(mid, other + (size_t)min(i0, n) * W + k0);
+        BV::load(dn, other + (size_t)(min(i0, n) + 1) * W + k0);
+        BV::load(f, hf + (size_t)min(i0, n) * W + k0);
+        auto edge = [&](int ic) {  // the west (k0-1) or east (k0+V) value of row ic
+            const size_t row = (size_t)ic * W;
+            if (((ic + C) & 1) == 0) return k0 > 0 ? other[row + k0 - 1] : T(0);
+            return k0 + V < kact ? other[row + k0 + V] : T(0);
+        };
+        T ew = edge(min(i0, n));
+        for (int r = 0; r < rb; ++r) {
+            const int i = i0 + r;
+            const bool live = has && i <= i1;
+            // past row n (last band only): a valid row of the same parity (n or n - 1, the
+            // ring row 0 when n = 1) for the steps that store nothing
+            const int ic = i <= n ? i : n - ((i - n) & 1);
+            const int in = i + 1 <= n ? i + 1 : n - ((i + 1 - n) & 1);
+            BV::load(dn2, other + (size_t)(in + 1) * W + k0);
+            BV::load(f2, hf + (size_t)in * W + k0);
+            const T ew2 = edge(in);
+            const int p = (ic + C) & 1;
+            const size_t row = (size_t)ic * W;
+            T res[V];
+            if (p == 0) {  // west/east at k-1, k
+#pragma unroll
+                for (int q = 0; q < V; ++q) res[q] = BV::update(f[q], up[q], dn[q], q ? mid[q - 1] : ew, mid[q]);
+            } else {  // at k, k+1
+#pragma unroll
+                for (int q = 0; q < V; ++q)
+                    res[q] = BV::update(f[q], up[q], dn[q], mid[q], q + 1 < V ? mid[q + 1] : ew);
+            }
+            if (live) {
+                const int j0 = 2 * k0 + p;  // natural column of value q: j0 + 2q
+                if (j0 >= 1 && j0 + 2 * (V - 1) <= n) {
+                    BV::store(self + row + k0, res);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < V; ++q)
+                        if (j0 + 2 * q >= 1 && j0 + 2 * q <= n) self[row + k0 + q] = res[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                up[q] = mid[q];
+                mid[q] = dn[q];
+                dn[q] = dn2[q];
+                f[q] = f2[q];
+            }
+            ew = ew2;
+        }
+    }
+}
+
+// One FP64 half-sweep of colour C over the whole problem by this block, one pair of
+// values per thread per iteration (flattened over rows and pairs: every thread busy,
+// which suits the FP64 pipe).  The loop trip count is uniform over the block (quarter()
+// votes across the warp).  Loads are ordinary (coherent) loads: the other colour was
+// written by this block one half-sweep earlier.
 template <int C, int THREADS>
 __device__ void block_half_sweep_f64(const DevProblem &P) {
     double *self = P.u[C];
@@ -95,8 +202,10 @@ __device__ void block_half_sweep_f64(const DevProblem &P) {
         const int i = 1 + qq / npairs, k0 = 2 * (qq % npairs);
         const int p = (i + C) & 1;
         const size_t row = (size_t)i * W;
-        const double2 up = ldg2(other + row - W + k0), mid = ldg2(other + row + k0);
-        const double2 dn = ldg2(other + row + W + k0), f2 = ldg2(hf + row + k0);
+        const double2 up = *reinterpret_cast<const double2 *>(other + row - W + k0);
+        const double2 mid = *reinterpret_cast<const double2 *>(other + row + k0);
+        const double2 dn = *reinterpret_cast<const double2 *>(other + row + W + k0);
+        const double2 f2 = *reinterpret_cast<const double2 *>(hf + row + k0);
         double w0, e0, w1, e1;
         if (p == 0) {
             w0 = k0 > 0 ? other[row + k0 - 1] : 0.0;
@@ -116,28 +225,7 @@ __device__ void block_half_sweep_f64(const DevProblem &P) {
 // FP32 half-sweep of the defect equation (h^2 f replaced by the scaled defect r).
 template <int C, int THREADS>
 __device__ void block_half_sweep_f32(const DevProblem &P) {
-    float *self = P.d[C];
-    const float *other = P.d[C ^ 1];
-    const float *hf = P.r[C];
-    const int n = P.n, W = P.W32, kact = kact_of(n);
-    const int items = n * kact;
-    for (int base = 0; base < items; base += THREADS) {
-        const int q = base + threadIdx.x;
-        if (q < items) {
-            const int i = 1 + q / kact, k = q % kact;
-            const int j = 2 * k + ((i + C) & 1);
-            if (j >= 1 && j <= n) {
-                const size_t row = (size_t)i * W;
-                const int p = (i + C) & 1;
-                const float vw = other[row + k - 1 + p], ve = other[row + k + p];
-                float s = __fadd_rn(hf[row + k], other[row - W + k]);
-                s = __fadd_rn(s, other[row + W + k]);
-                s = __fadd_rn(s, vw);
-                s = __fadd_rn(s, ve);
-                self[row + k] = __fmul_rn(s, 0.25f);
-            }
-        }
-    }
+    block_half_sweep_band<float, C, THREADS>(P.d[C], P.d[C ^ 1], P.r[C], P.n, P.W32);
 }
 
 // Per-thread partial of sum rt^2 (and max |rt|; optionally write (float)(rt * scale)).
