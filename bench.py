@@ -758,11 +758,16 @@ def main():
     with ClockSampler(str(uuid) if uuid else None) as clocks:
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(stream)
+        marks = []
         for _ in range(args.steps):
             rho = step(f, u0, out, record=True)
+            marks.append(torch.cuda.Event(enable_timing=True))
+            marks[-1].record(stream)
         t1.record(stream)
         barrier()
     elapsed = t0.elapsed_time(t1) / 1e3
+    step_ms = [a.elapsed_time(b) for a, b in zip([t0] + marks[:-1], marks)]
+    sweep_ms = [a.elapsed_time(b) for a, b in sweep_events]
     if world > 1:
         tt = torch.tensor([elapsed], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -870,6 +875,9 @@ def main():
             "clocks": clocks.summary(),
             "time_to_residual": ttr,
             "small_grid": small,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+            "sweeps_ms": {"min": min(sweep_ms), "median": statistics.median(sweep_ms), "max": max(sweep_ms),
+                          "note": "device time of the sweeps alone in each step"},
         }
         print(json.dumps(line))
     if world > 1:

@@ -232,13 +232,21 @@ __global__ void __launch_bounds__(kBiasThreads) bias_grad_kernel(const uint16_t 
     const int g = threadIdx.x % groups, r = threadIdx.x / groups;
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (r < lanes) {
-        for (long p = (long)blockIdx.x * lanes + r; p < P; p += (long)gridDim.x * lanes) {
-            const uint4 v = ld16(G + p * Cout + g * 8);
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        // four pixels per step, their loads issued together
+        const long stride = (long)gridDim.x * lanes;
+        for (long p = (long)blockIdx.x * lanes + r; p < P; p += 4 * stride) {
+            uint4 v[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                acc[2 * e] += __uint_as_float(w[e] << 16);
-                acc[2 * e + 1] += __uint_as_float(w[e] & 0xFFFF0000u);
+            for (int u = 0; u < 4; ++u)
+                v[u] = p + u * stride < P ? ld16(G + (p + u * stride) * Cout + g * 8) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    acc[2 * e] += __uint_as_float(w[e] << 16);
+                    acc[2 * e + 1] += __uint_as_float(w[e] & 0xFFFF0000u);
+                }
             }
         }
     }
@@ -311,7 +319,7 @@ rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t 
         RBGS_LAUNCH_CHECK();
     }
     if (db) {
-        bias_grad_kernel<<<8 * 152, kBiasThreads, 0, s>>>(G, db, P, Cout);
+        bias_grad_kernel<<<2 * 152, kBiasThreads, 0, s>>>(G, db, P, Cout);
         RBGS_LAUNCH_CHECK();
     }
     return RBGS_OK;
