@@ -66,8 +66,8 @@ def parse():
     p.add_argument("--conv-hw", type=int, default=256, help="conv: level-0 height = width")
     p.add_argument("--conv-layer", type=int, default=-1, help="conv: one layer index (-1: all 15)")
     p.add_argument("--conv-op", choices=["all", "fwd", "dgrad", "wgrad"], default="all")
-    p.add_argument("--engine", choices=["tcgen05", "mma_sync", "both"], default="both",
-                   help="conv: convolution engine(s) to time")
+    p.add_argument("--engine", choices=["tcgen05", "mma_sync", "tcgen05_gather", "both", "all"], default="both",
+                   help="conv: engine(s) to time (both: tcgen05 and mma_sync; all: the three)")
     p.add_argument("--mixed-n", type=int, default=8192, help="mixed: interior size")
     p.add_argument("--mixed-cap", type=int, default=20000, help="mixed: sweeps actually run per form")
     p.add_argument("--mixed-chunk", type=int, default=2000, help="mixed: sweeps between residual samples")
@@ -510,7 +510,7 @@ def run_conv(args):
                            dw=torch.zeros(cout, k, k, cin, device=dev), db=torch.zeros(cout, device=dev),
                            flop=2.0 * B * H * W * k * k * cin * cout))
 
-    def timed(ev, key, flop, fn):
+    def timed(ev, key, li, flop, fn):
         if ev is None:
             fn()
             return
@@ -518,29 +518,35 @@ def run_conv(args):
         e0.record(stream)
         fn()
         e1.record(stream)
-        ev.append((key, flop, e0, e1))
+        ev.append((key, li, flop, e0, e1))
 
     def step(ev=None):
         for L in layers:
+            li = L["i"]
             if "fwd" in ops:
-                timed(ev, "fwd", L["flop"], lambda: un.rbgs_conv_forward(L["x"], L["w"], L["bias"], L["y"], relu=True))
+                timed(ev, "fwd", li, L["flop"],
+                      lambda: un.rbgs_conv_forward(L["x"], L["w"], L["bias"], L["y"], relu=True))
             if "dgrad" in ops and L["dx"] is not None:
-                timed(ev, "dgrad", L["flop"], lambda: un.rbgs_conv_backward(L["x"], L["w"], L["g"], L["dx"], None, None))
+                timed(ev, "dgrad", li, L["flop"],
+                      lambda: un.rbgs_conv_backward(L["x"], L["w"], L["g"], L["dx"], None, None))
             if "wgrad" in ops:
-                timed(ev, "wgrad", L["flop"],
+                timed(ev, "wgrad", li, L["flop"],
                       lambda: un.rbgs_conv_backward(L["x"], L["w"], L["g"], None, L["dw"], None, accumulate=True))
                 un.rbgs_conv_backward(L["x"], L["w"], L["g"], None, None, L["db"], accumulate=True)
 
     flop = 0.0
     for L in layers:
         flop += L["flop"] * (("fwd" in ops) + ("dgrad" in ops and L["dx"] is not None) + ("wgrad" in ops))
-    engines = ("tcgen05", "mma_sync") if args.engine == "both" else (args.engine,)
+    engines = {"both": ("tcgen05", "mma_sync"), "all": ("tcgen05", "mma_sync", "tcgen05_gather")}.get(
+        args.engine, (args.engine,))
+    engine_ids = {"tcgen05": un.RBGS_CONV_TCGEN05, "mma_sync": un.RBGS_CONV_MMA_SYNC,
+                  "tcgen05_gather": un.RBGS_CONV_TCGEN05_GATHER}
     results = {}
     clocks = None
     peaks = measured_peaks() or {}
     peak = peaks.get("bf16_tflops", 1900.0)
     for name in engines:
-        un.rbgs_conv_set_engine(un.RBGS_CONV_TCGEN05 if name == "tcgen05" else un.RBGS_CONV_MMA_SYNC)
+        un.rbgs_conv_set_engine(engine_ids[name])
         for _ in range(args.warmup):
             step()
         un.rbgs_conv_check(dev)
@@ -558,14 +564,19 @@ def run_conv(args):
             torch.cuda.synchronize(dev)
         un.rbgs_conv_check(dev)
         t = e0.elapsed_time(e1) / 1e3 / args.steps
-        per = {}
-        for key, fl, a, b in ev:
+        per, per_layer = {}, {}
+        for key, li, fl, a, b in ev:
+            dt = a.elapsed_time(b) / 1e3
             acc = per.setdefault(key, [0.0, 0.0])
             acc[0] += fl
-            acc[1] += a.elapsed_time(b) / 1e3
+            acc[1] += dt
+            pl = per_layer.setdefault(f"{li}:{key}", [0.0, 0.0])
+            pl[0] += fl
+            pl[1] += dt
         results[name] = dict(tflops=flop / t / 1e12, ms_per_step=1e3 * t,
                              products={k: {"tflops": v[0] / v[1] / 1e12, "ms_per_step": 1e3 * v[1] / args.steps}
-                                       for k, v in per.items() if v[1] > 0})
+                                       for k, v in per.items() if v[1] > 0},
+                             per_layer_tflops={k: v[0] / v[1] / 1e12 for k, v in per_layer.items() if v[1] > 0})
         if name == engines[0]:
             clocks = sampler.summary()
     un.rbgs_conv_set_engine(un.RBGS_CONV_TCGEN05)

@@ -58,14 +58,19 @@ rbgs_status rbgs_conv_backward(const uint16_t *X, const uint16_t *Wt, const uint
 
 /*
  * Engine of the convolution kernels (process-wide; applies to the network too):
- *   RBGS_CONV_TCGEN05  (default) 5th-generation tensor cores: tcgen05.mma from shared-memory
- *                      descriptors, FP32 accumulators in tensor memory, 128-row tiles;
- *   RBGS_CONV_MMA_SYNC warp-level mma.sync tiles with register accumulators.
- * Both compute the same sums in FP32 (the order of accumulation differs).  Returns
+ *   RBGS_CONV_TCGEN05        (default) 5th-generation tensor cores: tcgen05.mma from shared-
+ *                            memory descriptors, FP32 accumulators in tensor memory, 128-row
+ *                            tiles; operand tiles of the data-gradient product loaded by TMA
+ *                            when the output channels split into chunks of 64, 32 and 16,
+ *                            all other operand tiles gathered by cp.async;
+ *   RBGS_CONV_MMA_SYNC       warp-level mma.sync tiles with register accumulators;
+ *   RBGS_CONV_TCGEN05_GATHER tcgen05 with every operand tile gathered by cp.async.
+ * All compute the same sums in FP32 (the order of accumulation differs).  Returns
  * RBGS_EINVAL for another value.  rbgs_conv_get_engine returns the current engine.
  */
 #define RBGS_CONV_TCGEN05 0
 #define RBGS_CONV_MMA_SYNC 1
+#define RBGS_CONV_TCGEN05_GATHER 2
 rbgs_status rbgs_conv_set_engine(int engine);
 int rbgs_conv_get_engine(void);
 

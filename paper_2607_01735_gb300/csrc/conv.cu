@@ -272,14 +272,14 @@ int g_engine = RBGS_CONV_TCGEN05;
 rbgs_status umma_conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y, int B, int H,
                               int W, int Cin, int Cout, int ks, int relu, int y_fp32, cudaStream_t s);
 rbgs_status umma_conv_backward_data(const uint16_t *Wtt, const uint16_t *G, float *dX, int B, int H, int W,
-                                    int Cin, int Cout, int ks, int accumulate, cudaStream_t s);
+                                    int Cin, int Cout, int ks, int accumulate, bool tma, cudaStream_t s);
 rbgs_status umma_conv_backward_weight(const uint16_t *X, const uint16_t *G, float *dW, int B, int H, int W,
                                       int Cin, int Cout, int ks, cudaStream_t s);
 rbgs_status umma_conv_check(cudaStream_t s);
 
 rbgs_status conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y, int B, int H,
                          int W, int Cin, int Cout, int ks, int relu, int y_fp32, cudaStream_t s) {
-    if (g_engine == RBGS_CONV_TCGEN05)
+    if (g_engine != RBGS_CONV_MMA_SYNC)
         return umma_conv_forward(X, Wt, bias, Y, B, H, W, Cin, Cout, ks, relu, y_fp32, s);
     ConvArgs a{X, Wt, nullptr, bias, Y, B, H, W, Cin, Cout, ks, relu, y_fp32, 0, 0};
     const long P = (long)B * H * W;
@@ -297,8 +297,9 @@ rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t 
     if (dX) {
         transpose_weights_kernel<<<256, 256, 0, s>>>(Wt, Wtt, Cout, taps, Cin);
         RBGS_LAUNCH_CHECK();
-        if (g_engine == RBGS_CONV_TCGEN05) {
-            const rbgs_status st = umma_conv_backward_data(Wtt, G, dX, B, H, W, Cin, Cout, ks, accumulate, s);
+        if (g_engine != RBGS_CONV_MMA_SYNC) {
+            const rbgs_status st = umma_conv_backward_data(Wtt, G, dX, B, H, W, Cin, Cout, ks, accumulate,
+                                                           g_engine == RBGS_CONV_TCGEN05, s);
             if (st != RBGS_OK) return st;
         } else {
             ConvArgs a{X, Wtt, G, nullptr, dX, B, H, W, Cin, Cout, ks, 0, 0, accumulate, 0};
@@ -307,7 +308,7 @@ rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t 
             RBGS_LAUNCH_CHECK();
         }
     }
-    if (dW && g_engine == RBGS_CONV_TCGEN05) {
+    if (dW && g_engine != RBGS_CONV_MMA_SYNC) {
         const rbgs_status st = umma_conv_backward_weight(X, G, dW, B, H, W, Cin, Cout, ks, s);
         if (st != RBGS_OK) return st;
     } else if (dW) {
@@ -360,7 +361,7 @@ extern "C" rbgs_status rbgs_conv_backward(const uint16_t *X, const uint16_t *Wt,
 
 extern "C" rbgs_status rbgs_conv_set_engine(int engine) {
     clear_error();
-    if (engine != RBGS_CONV_TCGEN05 && engine != RBGS_CONV_MMA_SYNC) {
+    if (engine != RBGS_CONV_TCGEN05 && engine != RBGS_CONV_MMA_SYNC && engine != RBGS_CONV_TCGEN05_GATHER) {
         set_error("rbgs_conv_set_engine: unknown engine %d", engine);
         return RBGS_EINVAL;
     }

@@ -37,7 +37,11 @@
 //     16 bytes at (j bn/8 + i) 128; LBO (next k group) = 16 bn B, SBO (next mn group) = 128 B.
 // The producer mapping puts the 8 threads of each quarter-warp on 8 different rows of
 // one chunk column, so their 16-byte writes fall in 8 distinct bank groups.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <cstring>
 
 #include "common.cuh"
 #include "tma.cuh"
@@ -608,6 +612,8 @@ rbgs_status launch(const UArgs &a, cudaStream_t s) {
 
 bool sizes_fit(int B, int H, int W) { return (long)B * H * W < (1L << 31) - UK; }
 
+#include "conv_tma.cuh"
+
 }  // namespace
 
 rbgs_status umma_conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y, int B, int H,
@@ -616,6 +622,8 @@ rbgs_status umma_conv_forward(const uint16_t *X, const uint16_t *Wt, const float
         set_error("tcgen05 convolution: at most 2^31 - 64 pixels");
         return RBGS_EINVAL;
     }
+    // (the TMA-fed kernel also takes the forward product, but measured slower there than
+    // the cp.async gathers: its weight box reads bn rows 9 Cin apart per tap)
     UArgs a{};
     a.X = X, a.Wt = Wt, a.bias = bias, a.out = Y;
     a.H = H, a.W = W, a.Cin = Cin, a.Cout = Cout, a.ks = ks, a.relu = relu, a.y_fp32 = y_fp32;
@@ -627,11 +635,14 @@ rbgs_status umma_conv_forward(const uint16_t *X, const uint16_t *Wt, const float
 }
 
 rbgs_status umma_conv_backward_data(const uint16_t *Wtt, const uint16_t *G, float *dX, int B, int H, int W,
-                                    int Cin, int Cout, int ks, int accumulate, cudaStream_t s) {
+                                    int Cin, int Cout, int ks, int accumulate, bool tma, cudaStream_t s) {
     if (!sizes_fit(B, H, W)) {
         set_error("tcgen05 convolution: at most 2^31 - 64 pixels");
         return RBGS_EINVAL;
     }
+    rbgs_status st = RBGS_OK;
+    if (tma && tma_conv_launch<U_BWD_DATA>(G, Wtt, nullptr, dX, B, H, W, Cin, Cout, ks, 0, 0, accumulate, s, &st))
+        return st;
     UArgs a{};
     a.Wt = Wtt, a.G = G, a.out = dX;
     a.H = H, a.W = W, a.Cin = Cin, a.Cout = Cout, a.ks = ks, a.accumulate = accumulate;

@@ -65,11 +65,14 @@ def _stream(t):
 
 RBGS_CONV_TCGEN05 = 0
 RBGS_CONV_MMA_SYNC = 1
+RBGS_CONV_TCGEN05_GATHER = 2
 
 
 def rbgs_conv_set_engine(engine: int) -> None:
     """Selects the convolution engine process-wide: RBGS_CONV_TCGEN05 (tensor memory
-    accumulators, default) or RBGS_CONV_MMA_SYNC (warp-level tiles)."""
+    accumulators, TMA-loaded operands where the channels allow; default),
+    RBGS_CONV_TCGEN05_GATHER (the same with cp.async-gathered operands) or
+    RBGS_CONV_MMA_SYNC (warp-level tiles)."""
     _check(_lib().rbgs_conv_set_engine(int(engine)))
 
 

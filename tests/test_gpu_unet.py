@@ -32,7 +32,7 @@ def _bf(a):
     return torch.from_numpy(a).to(torch.float32).to(torch.bfloat16)
 
 
-ENGINES = {"tcgen05": 0, "mma_sync": 1}
+ENGINES = {"tcgen05": 0, "mma_sync": 1, "tcgen05_gather": 2}
 
 # shapes: ragged pixel tiles (B H W not a multiple of 128), every N-tile width the
 # tcgen05 kernel picks (16 for Cout 8, 48, 192 for 384 = 2 x 192, 256), 1x1 kernels,
@@ -97,8 +97,9 @@ def test_conv_forward_and_backward_match_oracle(B, H, W, Cin, Cout, k, engine):
 
 @pytest.mark.parametrize("B,H,W,Cin,Cout,k", CONV_SHAPES[:6])
 def test_conv_engines_agree(B, H, W, Cin, Cout, k):
-    """tcgen05 (TMEM accumulators) and mma.sync (register accumulators) form the same FP32
-    sums of the same bf16 products: they differ by accumulation order only."""
+    """tcgen05 (TMEM accumulators; TMA-loaded or gathered operands) and mma.sync (register
+    accumulators) form the same FP32 sums of the same bf16 products: they differ by
+    accumulation order only."""
     from paper_2607_01735_gb300 import unet as un
     rng = np.random.default_rng(3 * Cin + Cout)
     x = _bf(rng.normal(size=(B, H, W, Cin))).cuda()
@@ -115,9 +116,10 @@ def test_conv_engines_agree(B, H, W, Cin, Cout, k):
         un.rbgs_conv_check()
         outs[name] = (y, dx, dw)
     un.rbgs_conv_set_engine(un.RBGS_CONV_TCGEN05)
-    for a, b in zip(outs["tcgen05"], outs["mma_sync"]):
-        scale = float(b.abs().max())
-        assert float((a - b).abs().max()) <= 1e-5 * scale + 1e-6
+    for other in ("tcgen05", "tcgen05_gather"):
+        for a, b in zip(outs[other], outs["mma_sync"]):
+            scale = float(b.abs().max())
+            assert float((a - b).abs().max()) <= 1e-5 * scale + 1e-6
 
 
 def test_network_gradient_matches_oracle(engine):
