@@ -16,10 +16,13 @@
 //   B: the 3D box of the weights for that tap and chunk, [Cout][taps][Cin] (forward) or
 //      the transposed [taps][Cin][Cout] (data gradient).
 // Roles: warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs (w/16 per stage) and
-// the commits, warps 2-5 drain the double-buffered TMEM accumulators (warp w reads lanes
-// 32 (w mod 4) ..).  Waits are bounded exactly as in the cp.async kernel.
+// the commits, warps 2-9 drain the double-buffered TMEM accumulators: warp w reads lanes
+// 32 (w mod 4) .. of every other 16-column slice (two warps per lane quarter, since with
+// few output channels the drain, not the MMAs, sets the pace).  Waits are bounded exactly
+// as in the cp.async kernel.
 
-constexpr int kTmaThreads = 192;
+constexpr int kTmaThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kTmaEpiThreads = 256;
 constexpr int kTmaMaxChunks = 8;
 constexpr uint32_t kTmaRing = 200 * 1024;
 
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull_bar[b], 1);
-            mbar_init(&tempty_bar[b], 128);
+            mbar_init(&tempty_bar[b], kTmaEpiThreads);
         }
         *abort_flag = 0;
         fence_barrier_init();
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             for (int tile = blockIdx.x; tile < a.num_tiles && live; tile += gridDim.x) {
                 const TTile T = decode_ttile(a, tile);
                 for (int kt = 0; kt < KT; ++kt) {
-                    if (!wait_or_abort(&empty_bar[s], ph ^ 1u, abort_flag)) {
+                    if (!wait_or_abort_spin(&empty_bar[s], ph ^ 1u, abort_flag)) {
                         live = false;
                         break;
                     }
@@ -163,11 +166,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             bool live = true;
             for (int tile = blockIdx.x; tile < a.num_tiles && live; tile += gridDim.x, ++local) {
                 const int buf = local & 1;
-                if (!wait_or_abort(&tempty_bar[buf], (((uint32_t)local >> 1) & 1u) ^ 1u, abort_flag)) break;
+                if (!wait_or_abort_spin(&tempty_bar[buf], (((uint32_t)local >> 1) & 1u) ^ 1u, abort_flag)) break;
                 tc_fence_after();
                 const uint32_t acc = tmem + (uint32_t)(buf * bn);
                 for (int kt = 0; kt < KT; ++kt) {
-                    if (!wait_or_abort(&full_bar[s], ph, abort_flag)) {
+                    if (!wait_or_abort_spin(&full_bar[s], ph, abort_flag)) {
                         live = false;
                         break;
                     }
@@ -194,7 +197,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             }
         }
     } else {
-        const int q = warp & 3;  // TMEM lane quarter
+        const int q = warp & 3;             // TMEM lane quarter
+        const int half = (warp - 2) >> 2;   // which 16-column slices: half, half + 2, ...
         const int row = q * 32 + lane;
         const int yy = row / a.tw, xx = row - yy * a.tw;
         int local = 0;
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) conv_tma_kernel(const __grid_c
             const bool pix = y < a.H && x < a.W;
             const long m = ((long)T.b * a.H + y) * a.W + x;
 #pragma unroll 1
-            for (int c0 = 0; c0 < bn; c0 += 16) {
+            for (int c0 = half * 16; c0 < bn; c0 += 32) {
                 uint32_t r[16];
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * bn + c0), r);
                 if (!pix) continue;

@@ -204,6 +204,18 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
     return false;
 }
 
+// Bounded wait by polling without a suspend hint, for the single threads (the TMA and MMA
+// issuers) whose hand-offs sit on the critical path of every stage.
+__device__ __forceinline__ bool wait_or_abort_spin(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    for (uint32_t q = 0; q < (1u << 22); ++q) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((q & 255u) == 255u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicOr(&g_conv_wait_failed, 1);
+    return false;
+}
+
 struct Tile {
     int m0, n0, kbeg, kend, KT;
 };
