@@ -44,6 +44,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "conv_wait.cuh"
 #include "tma.cuh"
 #include "../../include/rbgs_unet.h"
 
@@ -65,6 +66,7 @@ constexpr int kMaxStages = 10;
 constexpr int kLag = 2;                   // stages in flight per producer before it signals
 constexpr uint32_t kPolls = 4000;          // x kSuspendNs: a wait gives up after about 4 s
 constexpr uint32_t kSuspendNs = 1000000;  // each poll sleeps until the phase completes or 1 ms
+constexpr uint32_t kSpinPolls = 1u << 22; // spinning polls of the issuing threads
 constexpr int kMaxBn = 256;
 constexpr uint32_t kRingBudget = 200 * 1024;
 constexpr size_t kMaxSmem = kRingBudget + 1024;
@@ -179,41 +181,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// One poll that suspends the thread until the phase with `parity` completes, or until
-// kSuspendNs have passed, instead of spinning.
-__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait that also gives up as soon as another role has aborted.
+// The kernels' waits: suspending polls for the many-thread roles, spinning polls for the
+// single issuing threads (conv_wait.cuh).  A suspending wait gives up after about 4 s, a
+// spinning one after 2^22 polls, each of which blocks for a hardware-defined time slice.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    for (uint32_t q = 0; q < kPolls; ++q) {
-        if (mbar_try_wait_suspend(bar, parity)) return true;
-        if (*abort_flag) return false;
-    }
-    *abort_flag = 1;
-    atomicOr(&g_conv_wait_failed, 1);
-    return false;
+    return rbgs::wait_or_abort(bar, parity, abort_flag, kPolls, kSuspendNs, &g_conv_wait_failed);
 }
 
-// Bounded wait by polling without a suspend hint, for the single threads (the TMA and MMA
-// issuers) whose hand-offs sit on the critical path of every stage.
 __device__ __forceinline__ bool wait_or_abort_spin(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    for (uint32_t q = 0; q < (1u << 22); ++q) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((q & 255u) == 255u && *abort_flag) return false;
-    }
-    *abort_flag = 1;
-    atomicOr(&g_conv_wait_failed, 1);
-    return false;
+    return rbgs::wait_or_abort_spin(bar, parity, abort_flag, kSpinPolls, &g_conv_wait_failed);
 }
 
 struct Tile {

@@ -1,7 +1,13 @@
-// Test harness for the library's bounded mbarrier wait (csrc/tma.cuh): one kernel waits
-// on a barrier that nothing completes and must give up after `polls` polls and report
-// it; a control kernel arrives on the barrier first and must see it complete.
+// Test harness for the library's bounded mbarrier waits.
+//  * csrc/tma.cuh: one kernel waits on a barrier that nothing completes and must give up
+//    after `polls` polls and report it; a control kernel arrives on the barrier first
+//    and must see it complete.
+//  * csrc/conv_wait.cuh (the convolution kernels' abort protocol): one role spins on a
+//    barrier that nothing completes, another role waits (suspending) on a second barrier
+//    that nothing completes either.  The side with the short limit must give up and raise
+//    the abort flag; the other must leave through the flag, long before its own limit.
 // Test infrastructure only.
+#include "../../paper_2607_01735_gb300/csrc/conv_wait.cuh"
 #include "../../paper_2607_01735_gb300/csrc/tma.cuh"
 
 namespace {
@@ -21,7 +27,40 @@ __global__ void wait_kernel(unsigned polls, int arrive, int *status) {
     if (ok) atomicOr(status, 2);    // the barrier completed
 }
 
+// Thread 0 plays the single issuing thread (spinning wait, `polls` polls); warp 1 plays
+// the epilogue (suspending waits of at most 1 ms, `waiter_polls` of them).
+__global__ void abort_kernel(unsigned polls, unsigned waiter_polls, int *status, int *fail_issuer,
+                             int *fail_waiter) {
+    __shared__ uint64_t a, b;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        rbgs::mbar_init(&a, 1);
+        rbgs::mbar_init(&b, 1);
+        abort_flag = 0;
+        rbgs::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool ok = rbgs::wait_or_abort_spin(&a, 0, &abort_flag, polls, fail_issuer);
+        atomicOr(status, ok ? 4 : 1);  // 1: the issuer gave up
+    } else if (threadIdx.x >= 32) {
+        const bool ok = rbgs::wait_or_abort(&b, 0, &abort_flag, waiter_polls, 1000000u, fail_waiter);
+        atomicOr(status, ok ? 4 : 2);  // 2: a waiter left without completion
+    }
+}
+
 }  // namespace
+
+extern "C" int run_abort_check(unsigned polls, unsigned waiter_polls, int *out_host) {
+    int *d = nullptr;
+    if (cudaMalloc(&d, 3 * sizeof(int)) != cudaSuccess) return 1;
+    cudaMemset(d, 0, 3 * sizeof(int));
+    abort_kernel<<<1, 64>>>(polls, waiter_polls, d, d + 1, d + 2);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, d, 3 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? 0 : 2;
+}
 
 extern "C" int run_wait_check(unsigned polls, int arrive, int *status_host) {
     int *d = nullptr;
