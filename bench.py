@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--nprob", type=int, default=512)
     p.add_argument("--sizes", default="63,127,255,511,1023", help="batched: allowed interior sizes")
     p.add_argument("--tol", type=float, default=1e-8, help="batched: relative residual target")
+    p.add_argument("--team", type=int, default=0,
+                   help="batched: 0 autotuned, 1 one block per problem, 2/4 phased plan with clusters")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-ttr", action="store_true", help="skip the time-to-residual comparison")
@@ -348,7 +350,7 @@ def run_batched(args):
         outs.append(torch.empty_like(probs[-1][3]))
     refine = args.precision == "refine"
     opts = rb.default_opts(precision=rb.RBGS_FP32_REFINE if refine else rb.RBGS_FP64,
-                           inner_sweeps=args.inner, check_every=100)
+                           inner_sweeps=args.inner, check_every=100, team_size=args.team)
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):  # warm-up (includes the launch-shape autotuning)
         rb.rbgs_solve_batched(probs, args.tol, outs, opts, allow_failures=True)
@@ -382,7 +384,9 @@ def run_batched(args):
                 "converged": ok, "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                                  "p99": float(np.percentile(lat, 99)),
                                                  "max": float(lat.max())},
-                "glups": lups / t / 1e9, "total_sweeps": int(sum(r["sweeps"] for r in allres.values()))}
+                "glups": lups / t / 1e9, "total_sweeps": int(sum(r["sweeps"] for r in allres.values())),
+                "launch_shape": rb.rbgs_batched_last_shape(),
+                "step_s": [round(x, 4) for x in times]}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

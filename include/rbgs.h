@@ -77,6 +77,10 @@ typedef struct {
     int int_rows;      /* FP64 hybrid half-sweep: between strips of tile_rows rows whose adds run on
                           the FP64 pipe, strips of int_rows rows whose adds run as exact integer
                           IEEE additions (same results; 0: off, -1: automatic)                  */
+    int team_size;     /* rbgs_solve_batched: 2 or 4 forces the phased plan, in which the largest
+                          problems left over after full waves of one block per problem are each
+                          solved by a thread-block cluster of team_size blocks; 1: one block per
+                          problem always; 0: the autotuner decides                              */
 } rbgs_opts;
 
 /* Fills *opts with the defaults (all automatic). */
@@ -134,14 +138,17 @@ typedef struct {
 
 /*
  * Solves nprob independent problems of uneven sizes (1 <= N_p <= 32768) to rho <= tol each,
- * in one persistent launch captured with the packing and unpacking in a CUDA graph.  A
+ * in persistent launches captured with the packing and unpacking in a CUDA graph.  A
  * thread block claims one problem at a time, largest first, and solves it on its own
  * (FP64 sweeps with a residual check every opts->check_every sweeps, or, with
  * RBGS_FP32_REFINE, the mixed-precision refinement with opts->inner_sweeps FP32 sweeps per
  * correction), so each problem's iterate equals a single-problem solve with the same
- * options.  The launch shape (threads per block, blocks per SM) is picked by a built-in
- * autotuner on first use for a given size mix, unless opts->tile_rows (> 0: 256, 512 or
- * 1024 threads) and opts->tblock_k (blocks per SM) fix it.  u_out[p] receives problem p's
+ * options.  In the phased plan (opts->team_size) the largest problems that would otherwise
+ * run in a last, partly filled wave are each solved by a cluster of 2 or 4 blocks on as many
+ * SMs, with the same iterate.  The launch shape (threads per block, blocks per SM, team
+ * size) is picked by a built-in autotuner on first use for a given size mix, unless
+ * opts->team_size (> 1), or opts->tile_rows (> 0: 256, 512 or 1024 threads) and
+ * opts->tblock_k (blocks per SM), fix it.  u_out[p] receives problem p's
  * solution ((N_p+2)^2 values, device or host memory); res[p] its outcome, latency_ms
  * measured on the device from the batch's first problem start to this problem's end.
  * Returns RBGS_OK when every problem converged, else the first failing status.
@@ -150,6 +157,14 @@ typedef struct {
 rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, double tol,
                                const rbgs_opts *opts, void *cuda_stream, double **u_out,
                                rbgs_result *res);
+
+/*
+ * Launch shape of the last rbgs_solve_batched call on this thread (zeros before the first):
+ * threads per block, blocks per SM, team size (1: one block per problem; 2 or 4: the phased
+ * plan), and for the phased plan the number of largest problems solved one per block in its
+ * first phase and the number solved by clusters in its second.  Any pointer may be NULL.
+ */
+void rbgs_batched_last_shape(int *threads, int *blocks_per_sm, int *team, int *first, int *nteam);
 
 /*
  * Relative residual of a natural-layout iterate without allocating memory.  The paper has

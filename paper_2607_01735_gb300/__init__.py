@@ -30,7 +30,7 @@ RBGS_KERNEL_AUTO, RBGS_KERNEL_COLOUR, RBGS_KERNEL_TEMPORAL, RBGS_KERNEL_WAVEFRON
 # Every symbol include/rbgs.h declares.
 EXPORTED = ("rbgs_default_opts", "rbgs_create", "rbgs_sweep", "rbgs_residual", "rbgs_solve",
             "rbgs_get_solution", "rbgs_set_solution", "rbgs_solve_batched", "rbgs_destroy",
-            "rbgs_last_error", "rbgs_residual_static")
+            "rbgs_last_error", "rbgs_residual_static", "rbgs_batched_last_shape")
 
 
 class RbgsError(RuntimeError):
@@ -46,7 +46,8 @@ class Opts(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("max_sweeps", ctypes.c_long),
                 ("tblock_k", ctypes.c_int), ("tile_rows", ctypes.c_int),
                 ("fp64_emulate", ctypes.c_int), ("inner_sweeps", ctypes.c_int),
-                ("sweep_values", ctypes.c_int), ("sweep_rows", ctypes.c_int), ("int_rows", ctypes.c_int)]
+                ("sweep_values", ctypes.c_int), ("sweep_rows", ctypes.c_int), ("int_rows", ctypes.c_int),
+                ("team_size", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -96,6 +97,8 @@ def load_library(path: str | None = None):
     lib.rbgs_residual_static.restype = c_int
     lib.rbgs_last_error.argtypes = []
     lib.rbgs_last_error.restype = ctypes.c_char_p
+    lib.rbgs_batched_last_shape.argtypes = [ctypes.POINTER(c_int)] * 5
+    lib.rbgs_batched_last_shape.restype = None
     _lib = lib
     return lib
 
@@ -202,6 +205,13 @@ def rbgs_solve_batched(problems, tol: float, u_out: list, opts: Opts | None = No
         _check(st)
     return [{"status": r.status, "sweeps": r.sweeps, "rel": r.rel, "latency_ms": r.latency_ms}
             for r in res[:k]]
+
+
+def rbgs_batched_last_shape() -> dict:
+    """rbgs_batched_last_shape: launch shape of this thread's last batched solve."""
+    v = [ctypes.c_int(0) for _ in range(5)]
+    load_library().rbgs_batched_last_shape(*[ctypes.byref(x) for x in v])
+    return dict(zip(("threads", "blocks_per_sm", "team", "first", "nteam"), (x.value for x in v)))
 
 
 def rbgs_residual_static(n: int, h2: float, f, u, rel_out, stream=None) -> None:

@@ -54,47 +54,111 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-// Block-wide deterministic sum/max, result broadcast to every thread.
-template <int THREADS>
-__device__ __forceinline__ double bcast_sum(double v, double *smem) {
+// ---- teams.  A problem is solved by a team: one thread block, or the CS blocks of one
+// thread-block cluster (one block per SM).  The team's VT = CS * THREADS threads act as one
+// block: thread vt = rank * THREADS + threadIdx.x takes every VT-th work item, a team
+// barrier separates the colour phases, and reductions combine the blocks' partials in
+// rank order, so every block of the team sees the same residual and takes the same
+// decisions (the same number of barriers on every path).
+
+__device__ __forceinline__ int cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+
+// Barrier over the team: the block for CS = 1, else the cluster barrier with release /
+// acquire at cluster scope, which makes every global write of the team made before it
+// visible to every thread of the team after it.  Reached by all threads of the team on
+// the same paths (decisions come from team-wide values only).
+template <int CS>
+__device__ __forceinline__ void team_sync() {
+    if (CS == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+}
+
+// Shared-memory value of block `rank` of this cluster (distributed shared memory).
+__device__ __forceinline__ uint32_t dsmem_addr(const void *local, int rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    return ra;
+}
+__device__ __forceinline__ double ld_dsmem(const double *local, int rank) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_dsmem(const int *local, int rank) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(dsmem_addr(local, rank)) : "memory");
+    return v;
+}
+
+// Load of an array that other blocks of the team write: through L2 only for teams of
+// several blocks (an L1 line of this SM may predate the last team barrier).
+template <int CS, typename V>
+__device__ __forceinline__ V ldt(const V *p) {
+    if (CS == 1) return *p;
+    return __ldcg(p);
+}
+
+// Team-wide deterministic sum / max, the same value in every thread of the team: block
+// reduction (fixed tree), then the blocks' results added in rank order.
+template <int THREADS, int CS>
+__device__ __forceinline__ double team_sum(double v, double *smem, double *slot) {
     const double t = block_sum<THREADS>(v, smem);
-    __syncthreads();
-    if (threadIdx.x == 0) smem[0] = t;
-    __syncthreads();
-    const double r = smem[0];
-    __syncthreads();
+    if (threadIdx.x == 0) *slot = t;
+    team_sync<CS>();
+    double r;
+    if (CS == 1) {
+        r = *slot;
+    } else {
+        r = ld_dsmem(slot, 0);
+        for (int q = 1; q < CS; ++q) r = __dadd_rn(r, ld_dsmem(slot, q));
+    }
+    team_sync<CS>();
     return r;
 }
 
-template <int THREADS>
-__device__ __forceinline__ double bcast_max(double v, double *smem) {
+template <int THREADS, int CS>
+__device__ __forceinline__ double team_max(double v, double *smem, double *slot) {
     const double t = block_max<THREADS>(v, smem);
-    __syncthreads();
-    if (threadIdx.x == 0) smem[0] = t;
-    __syncthreads();
-    const double r = smem[0];
-    __syncthreads();
+    if (threadIdx.x == 0) *slot = t;
+    team_sync<CS>();
+    double r;
+    if (CS == 1) {
+        r = *slot;
+    } else {
+        r = ld_dsmem(slot, 0);
+        for (int q = 1; q < CS; ++q) r = fmax(r, ld_dsmem(slot, q));
+    }
+    team_sync<CS>();
     return r;
 }
 
 __device__ __forceinline__ int kact_of(int n) { return (((n + 3) / 2) + 1) & ~1; }
 
-// FP32 half-sweep of colour C over the whole problem by this block, as a row-band walk:
+// FP32 half-sweep of colour C over the whole problem by this team, as a row-band walk:
 // work item (column group g, band b) is a strip of V values (16 bytes) of the colour rows
 // walked down the band's rows with the other colour's rows i-1, i, i+1 in registers, so
 // each row of the other colour is loaded once per item (plus the band edges) and h2f once.
 // The west/east value that lies outside the item is read directly.  Loads are ordinary
-// (coherent) loads: the other colour was written by this block one half-sweep earlier.
-// Every thread of the block runs the same number of row steps, on rows of the same parity
-// (the FP64 quarter votes across the warp); steps past an item's band, and threads without
-// an item, compute on a valid row and store nothing.
+// (coherent) loads, through L2 for multi-block teams: the other colour was written by the
+// team one half-sweep earlier.  Every thread of the team runs the same number of row
+// steps, on rows of the same parity; steps past an item's band, and threads without an
+// item, compute on a valid row and store nothing (warps without any item skip the pass).
 template <typename T>
 struct BandVec;
 template <>
 struct BandVec<float> {
     static constexpr int V = 4;
+    template <int CS>
     __device__ static void load(float *v, const float *p) {
-        const float4 t = *reinterpret_cast<const float4 *>(p);
+        const float4 t = ldt<CS>(reinterpret_cast<const float4 *>(p));
         v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
     }
     __device__ static void store(float *p, const float *v) {
@@ -108,36 +172,36 @@ struct BandVec<float> {
         return __fmul_rn(s, 0.25f);
     }
 };
-template <typename T, int C, int THREADS>
-__device__ void block_half_sweep_band(T *__restrict__ self, const T *other, const T *__restrict__ hf, int n,
-                                      int W) {
+template <typename T, int C, int VT, int CS>
+__device__ void block_half_sweep_band(T *__restrict__ self, const T *other, const T *hf, int n, int W, int vt) {
     using BV = BandVec<T>;
     constexpr int V = BV::V;
     const int kact = kact_of(n);
     const int ncol = (kact + V - 1) / V;
-    const int bands = ncol < THREADS ? THREADS / ncol : 1;
+    const int bands = ncol < VT ? VT / ncol : 1;
     // rows per band, even: every band starts on an odd row, so at each step all bands sit
-    // on rows of one parity and the colour-offset branch (and the FP64 quarter's warp vote
-    // inside it) stays uniform across a warp that spans two bands
+    // on rows of one parity and the colour-offset branch stays uniform across a warp that
+    // spans two bands
     const int rb = ((n + bands - 1) / bands + 1) & ~1;
-    const int passes = (ncol * bands + THREADS - 1) / THREADS;  // > 1 only when ncol > THREADS
+    const int passes = (ncol * bands + VT - 1) / VT;  // > 1 only when ncol > VT
     for (int pass = 0; pass < passes; ++pass) {
-        const int item = pass * THREADS + threadIdx.x;
+        const int item = pass * VT + vt;
         const bool has = item < ncol * bands;
+        if (__all_sync(0xffffffffu, !has)) continue;  // warp-uniform: no item in this warp
         const int g = has ? item % ncol : 0, b = has ? item / ncol : 0;
         const int k0 = V * g;
         const int i0 = 1 + b * rb, i1 = min(n, i0 + rb - 1);
         // rows i-1, i, i+1 of the other colour and h2f of row i, plus the next step's row
         // i+2 / h2f i+1 / edge values loaded one step ahead (their latency overlaps a step)
         T up[V], mid[V], dn[V], f[V], dn2[V], f2[V];
-        BV::load(up, other + (size_t)min(i0 - 1, n) * W + k0);
-        BV::load(mid, other + (size_t)min(i0, n) * W + k0);
-        BV::load(dn, other + (size_t)(min(i0, n) + 1) * W + k0);
-        BV::load(f, hf + (size_t)min(i0, n) * W + k0);
+        BV::template load<CS>(up, other + (size_t)min(i0 - 1, n) * W + k0);
+        BV::template load<CS>(mid, other + (size_t)min(i0, n) * W + k0);
+        BV::template load<CS>(dn, other + (size_t)(min(i0, n) + 1) * W + k0);
+        BV::template load<CS>(f, hf + (size_t)min(i0, n) * W + k0);
         auto edge = [&](int ic) {  // the west (k0-1) or east (k0+V) value of row ic
             const size_t row = (size_t)ic * W;
-            if (((ic + C) & 1) == 0) return k0 > 0 ? other[row + k0 - 1] : T(0);
-            return k0 + V < kact ? other[row + k0 + V] : T(0);
+            if (((ic + C) & 1) == 0) return k0 > 0 ? ldt<CS>(other + row + k0 - 1) : T(0);
+            return k0 + V < kact ? ldt<CS>(other + row + k0 + V) : T(0);
         };
         T ew = edge(min(i0, n));
         for (int r = 0; r < rb; ++r) {
@@ -147,8 +211,8 @@ __device__ void block_half_sweep_band(T *__restrict__ self, const T *other, cons
             // ring row 0 when n = 1) for the steps that store nothing
             const int ic = i <= n ? i : n - ((i - n) & 1);
             const int in = i + 1 <= n ? i + 1 : n - ((i + 1 - n) & 1);
-            BV::load(dn2, other + (size_t)(in + 1) * W + k0);
-            BV::load(f2, hf + (size_t)in * W + k0);
+            BV::template load<CS>(dn2, other + (size_t)(in + 1) * W + k0);
+            BV::template load<CS>(f2, hf + (size_t)in * W + k0);
             const T ew2 = edge(in);
             const int p = (ic + C) & 1;
             const size_t row = (size_t)ic * W;
@@ -183,36 +247,38 @@ __device__ void block_half_sweep_band(T *__restrict__ self, const T *other, cons
     }
 }
 
-// One FP64 half-sweep of colour C over the whole problem by this block, one pair of
-// values per thread per iteration (flattened over rows and pairs: every thread busy,
-// which suits the FP64 pipe).  The loop trip count is uniform over the block (quarter()
-// votes across the warp).  Loads are ordinary (coherent) loads: the other colour was
-// written by this block one half-sweep earlier.
-template <int C, int THREADS>
-__device__ void block_half_sweep_f64(const DevProblem &P) {
+// One FP64 half-sweep of colour C over the whole problem by this team, one pair of values
+// per thread per iteration (flattened over rows and pairs: every thread busy, which suits
+// the FP64 pipe).  quarter() votes across the warp, so a warp runs an iteration whenever
+// any of its lanes has an item and leaves the loop as a whole.  Loads of the other colour
+// are ordinary (coherent) loads, through L2 for multi-block teams: the team wrote it one
+// half-sweep earlier.
+template <int C, int VT, int CS>
+__device__ void block_half_sweep_f64(const DevProblem &P, int vt) {
     double *self = P.u[C];
     const double *other = P.u[C ^ 1];
     const double *hf = P.hf[C];
     const int n = P.n, W = P.W, kact = kact_of(n), npairs = kact / 2;
     const int items = n * npairs;
-    for (int base = 0; base < items; base += THREADS) {
-        const int q = base + threadIdx.x;
+    for (int base = 0; base < items; base += VT) {
+        if (base + (vt & ~31) >= items) break;  // warp-uniform: no item left for this warp
+        const int q = base + vt;
         const bool act = q < items;
         const int qq = act ? q : 0;
         const int i = 1 + qq / npairs, k0 = 2 * (qq % npairs);
         const int p = (i + C) & 1;
         const size_t row = (size_t)i * W;
-        const double2 up = *reinterpret_cast<const double2 *>(other + row - W + k0);
-        const double2 mid = *reinterpret_cast<const double2 *>(other + row + k0);
-        const double2 dn = *reinterpret_cast<const double2 *>(other + row + W + k0);
+        const double2 up = ldt<CS>(reinterpret_cast<const double2 *>(other + row - W + k0));
+        const double2 mid = ldt<CS>(reinterpret_cast<const double2 *>(other + row + k0));
+        const double2 dn = ldt<CS>(reinterpret_cast<const double2 *>(other + row + W + k0));
         const double2 f2 = *reinterpret_cast<const double2 *>(hf + row + k0);
         double w0, e0, w1, e1;
         if (p == 0) {
-            w0 = k0 > 0 ? other[row + k0 - 1] : 0.0;
+            w0 = k0 > 0 ? ldt<CS>(other + row + k0 - 1) : 0.0;
             e0 = mid.x; w1 = mid.x; e1 = mid.y;
         } else {
             w0 = mid.x; e0 = mid.y; w1 = mid.y;
-            e1 = (k0 + 2 < kact) ? other[row + k0 + 2] : 0.0;
+            e1 = (k0 + 2 < kact) ? ldt<CS>(other + row + k0 + 2) : 0.0;
         }
         const double r0 = update_f64<false>(0, f2.x, up.x, dn.x, w0, e0, 1.0);
         const double r1 = update_f64<false>(0, f2.y, up.y, dn.y, w1, e1, 1.0);
@@ -223,31 +289,31 @@ __device__ void block_half_sweep_f64(const DevProblem &P) {
 }
 
 // FP32 half-sweep of the defect equation (h^2 f replaced by the scaled defect r).
-template <int C, int THREADS>
-__device__ void block_half_sweep_f32(const DevProblem &P) {
-    block_half_sweep_band<float, C, THREADS>(P.d[C], P.d[C ^ 1], P.r[C], P.n, P.W32);
+template <int C, int VT, int CS>
+__device__ void block_half_sweep_f32(const DevProblem &P, int vt) {
+    block_half_sweep_band<float, C, VT, CS>(P.d[C], P.d[C ^ 1], P.r[C], P.n, P.W32, vt);
 }
 
 // Per-thread partial of sum rt^2 (and max |rt|; optionally write (float)(rt * scale)).
-template <int THREADS, bool WRITE>
-__device__ void block_residual(const DevProblem &P, double scale, double &r2, double &mx) {
+template <int VT, int CS, bool WRITE>
+__device__ void block_residual(const DevProblem &P, double scale, double &r2, double &mx, int vt) {
     const int n = P.n, W = P.W, kact = kact_of(n);
     r2 = 0.0;
     mx = 0.0;
     for (int c = 0; c < 2; ++c) {
         const double *self = P.u[c], *other = P.u[c ^ 1], *hf = P.hf[c];
         const int items = n * kact;
-        for (int q = threadIdx.x; q < items; q += THREADS) {
+        for (int q = vt; q < items; q += VT) {
             const int i = 1 + q / kact, k = q % kact;
             const int p = (i + c) & 1;
             const int j = 2 * k + p;
             if (j < 1 || j > n) continue;
             const size_t row = (size_t)i * W;
-            double s = __dadd_rn(hf[row + k], other[row - W + k]);
-            s = __dadd_rn(s, other[row + W + k]);
-            s = __dadd_rn(s, other[row + k - 1 + p]);
-            s = __dadd_rn(s, other[row + k + p]);
-            const double r = __dadd_rn(s, -__dmul_rn(4.0, self[row + k]));
+            double s = __dadd_rn(hf[row + k], ldt<CS>(other + row - W + k));
+            s = __dadd_rn(s, ldt<CS>(other + row + W + k));
+            s = __dadd_rn(s, ldt<CS>(other + row + k - 1 + p));
+            s = __dadd_rn(s, ldt<CS>(other + row + k + p));
+            const double r = __dadd_rn(s, -__dmul_rn(4.0, ldt<CS>(self + row + k)));
             r2 = __fma_rn(r, r, r2);
             mx = fmax(mx, fabs(r));
             if (WRITE) P.r[c][(size_t)i * P.W32 + k] = __double2float_rn(__dmul_rn(r, scale));
@@ -255,13 +321,14 @@ __device__ void block_residual(const DevProblem &P, double scale, double &r2, do
     }
 }
 
-// sum (h^2 b)^2: h2f plus the ring neighbours, as in rhs_norm_kernel.
-template <int THREADS>
-__device__ double block_rhs_norm2(const DevProblem &P, double *smem) {
+// Per-thread partial of sum (h^2 b)^2: h2f plus the ring neighbours, as in rhs_norm_kernel
+// (the ring is never written, h2f only by the packing kernel).
+template <int VT>
+__device__ double rhs_norm2_partial(const DevProblem &P, int vt) {
     const int n = P.n, W = P.W;
     double acc = 0.0;
     const int total = n * n;
-    for (int q = threadIdx.x; q < total; q += THREADS) {
+    for (int q = vt; q < total; q += VT) {
         const int i = 1 + q / n, j = 1 + q % n;
         auto at = [&](const double *const *a, int ii, int jj) { return a[(ii + jj) & 1][(size_t)ii * W + (jj >> 1)]; };
         double b = at(P.hf, i, j);
@@ -271,22 +338,32 @@ __device__ double block_rhs_norm2(const DevProblem &P, double *smem) {
         if (j == n) b = __dadd_rn(b, at(P.u, i, n + 1));
         acc = __fma_rn(b, b, acc);
     }
-    return bcast_sum<THREADS>(acc, smem);
+    return acc;
 }
 
 __device__ __forceinline__ double rho_of(double r2, double den2) {
     return den2 > 0.0 ? sqrt(r2) / sqrt(den2) : sqrt(r2);
 }
 
-template <int THREADS>
+// Solve one problem with a team of CS blocks (rank: this block's place in it).  The sweep
+// limit is max_sweeps, scaled by (n / cap_n)^2 when cap_n > 0 (the autotuner's probes: the
+// work per problem then grows like n^4, as in a solve to tolerance).
+template <int THREADS, int CS>
 __device__ void solve_problem(const DevProblem &P, DevResult &R, double tol, int check_every,
-                              long long max_sweeps, int inner, bool refine, double *smem) {
+                              long long max_sweeps, int inner, bool refine, int cap_n, int rank, double *smem,
+                              double *slot) {
+    constexpr int VT = THREADS * CS;
+    const int vt = rank * THREADS + (int)threadIdx.x;
     const unsigned long long t0 = globaltimer();
-    const double den2 = block_rhs_norm2<THREADS>(P, smem);
+    if (cap_n > 0) {
+        const double frac = ((double)P.n * P.n) / ((double)cap_n * cap_n);
+        max_sweeps = max(1LL, (long long)(frac * (double)max_sweeps));
+    }
+    const double den2 = team_sum<THREADS, CS>(rhs_norm2_partial<VT>(P, vt), smem, slot);
     double r2, mx;
-    block_residual<THREADS, false>(P, 1.0, r2, mx);
-    r2 = bcast_sum<THREADS>(r2, smem);
-    mx = bcast_max<THREADS>(mx, smem);
+    block_residual<VT, CS, false>(P, 1.0, r2, mx, vt);
+    r2 = team_sum<THREADS, CS>(r2, smem, slot);
+    mx = team_max<THREADS, CS>(mx, smem, slot);
     double rho = rho_of(r2, den2);
     long long done = 0;
     while (!(rho <= tol) && done < max_sweeps && isfinite(rho)) {
@@ -294,10 +371,10 @@ __device__ void solve_problem(const DevProblem &P, DevResult &R, double tol, int
             long long k = check_every;
             if (k > max_sweeps - done) k = max_sweeps - done;
             for (long long it = 0; it < k; ++it) {
-                block_half_sweep_f64<0, THREADS>(P);
-                __syncthreads();
-                block_half_sweep_f64<1, THREADS>(P);
-                __syncthreads();
+                block_half_sweep_f64<0, VT, CS>(P, vt);
+                team_sync<CS>();
+                block_half_sweep_f64<1, VT, CS>(P, vt);
+                team_sync<CS>();
             }
             done += k;
         } else {
@@ -305,41 +382,41 @@ __device__ void solve_problem(const DevProblem &P, DevResult &R, double tol, int
             frexp(mx, &e);
             const double down = ldexp(1.0, -e), up = ldexp(1.0, e);
             double t2, tm;
-            block_residual<THREADS, true>(P, down, t2, tm);  // writes the scaled defect
+            block_residual<VT, CS, true>(P, down, t2, tm, vt);  // writes the scaled defect
             const size_t elems = (size_t)(P.n + 2) * P.W32;
-            for (size_t q = threadIdx.x; q < elems; q += THREADS) {
+            for (size_t q = vt; q < elems; q += VT) {
                 P.d[0][q] = 0.0f;
                 P.d[1][q] = 0.0f;
             }
-            __syncthreads();
+            team_sync<CS>();
             long long k = inner;
             if (k > max_sweeps - done) k = max_sweeps - done;
             for (long long it = 0; it < k; ++it) {
-                block_half_sweep_f32<0, THREADS>(P);
-                __syncthreads();
-                block_half_sweep_f32<1, THREADS>(P);
-                __syncthreads();
+                block_half_sweep_f32<0, VT, CS>(P, vt);
+                team_sync<CS>();
+                block_half_sweep_f32<1, VT, CS>(P, vt);
+                team_sync<CS>();
             }
             // u += (double)d * 2^e at interior points
             const int n = P.n, kact = kact_of(n);
             for (int c = 0; c < 2; ++c) {
-                for (int q = threadIdx.x; q < n * kact; q += THREADS) {
+                for (int q = vt; q < n * kact; q += VT) {
                     const int i = 1 + q / kact, kk = q % kact;
                     const int j = 2 * kk + ((i + c) & 1);
                     if (j < 1 || j > n) continue;
-                    double &uu = P.u[c][(size_t)i * P.W + kk];
-                    uu = __dadd_rn(uu, __dmul_rn((double)P.d[c][(size_t)i * P.W32 + kk], up));
+                    double *uu = P.u[c] + (size_t)i * P.W + kk;
+                    *uu = __dadd_rn(ldt<CS>(uu), __dmul_rn((double)ldt<CS>(P.d[c] + (size_t)i * P.W32 + kk), up));
                 }
             }
-            __syncthreads();
+            team_sync<CS>();
             done += k;
         }
-        block_residual<THREADS, false>(P, 1.0, r2, mx);
-        r2 = bcast_sum<THREADS>(r2, smem);
-        mx = bcast_max<THREADS>(mx, smem);
+        block_residual<VT, CS, false>(P, 1.0, r2, mx, vt);
+        r2 = team_sum<THREADS, CS>(r2, smem, slot);
+        mx = team_max<THREADS, CS>(mx, smem, slot);
         rho = rho_of(r2, den2);
     }
-    if (threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
         R.status = !isfinite(rho) ? RBGS_ENONFINITE : (rho <= tol ? RBGS_OK : RBGS_ENOTCONV);
         R.sweeps = done;
         R.rel = rho;
@@ -348,22 +425,43 @@ __device__ void solve_problem(const DevProblem &P, DevResult &R, double tol, int
     }
 }
 
-template <int THREADS>
+// Persistent solver over problems order[0 .. nprob).  The first nteam of them (the
+// largest) are solved by teams of CS blocks: block rank 0 of a cluster claims the next one
+// from queues[0] and the cluster solves it together.  After that every block claims the
+// rest one at a time from queues[1] and solves each on its own; no block waits on a block
+// outside its cluster, and a cluster's blocks part only after their last team barrier.
+template <int THREADS, int CS>
 __global__ void __launch_bounds__(THREADS)
 batched_persistent_kernel(const DevProblem *__restrict__ probs, DevResult *__restrict__ res,
-                          const int *__restrict__ order, int nprob, int *queue, double tol,
-                          int check_every, long long max_sweeps, int inner, int refine) {
+                          const int *__restrict__ order, int nprob, int nteam, int *queues, double tol,
+                          int check_every, long long max_sweeps, int inner, int refine, int cap_n) {
     __shared__ double smem[THREADS / 32 + 1];
+    __shared__ double slot;
     __shared__ int s_q;
+    if (CS > 1) {
+        const int rank = cluster_rank();
+        for (;;) {
+            if (rank == 0 && threadIdx.x == 0) s_q = atomicAdd(&queues[0], 1);
+            team_sync<CS>();
+            const int q = ld_dsmem(&s_q, 0);
+            team_sync<CS>();  // every block has read the claim before it is replaced
+            if (q >= nteam) break;
+            const int p = order[q];
+            const DevProblem P = probs[p];
+            solve_problem<THREADS, CS>(P, res[p], tol, check_every, max_sweeps, inner, refine != 0, cap_n, rank,
+                                       smem, &slot);
+        }
+    }
     for (;;) {
-        if (threadIdx.x == 0) s_q = atomicAdd(queue, 1);
+        if (threadIdx.x == 0) s_q = atomicAdd(&queues[1], 1);
         __syncthreads();
-        const int q = s_q;
+        const int q = (CS > 1 ? nteam : 0) + s_q;
         __syncthreads();
         if (q >= nprob) break;
         const int p = order[q];
         const DevProblem P = probs[p];
-        solve_problem<THREADS>(P, res[p], tol, check_every, max_sweeps, inner, refine != 0, smem);
+        solve_problem<THREADS, 1>(P, res[p], tol, check_every, max_sweeps, inner, refine != 0, cap_n, 0, smem,
+                                  &slot);
         __syncthreads();
     }
 }
@@ -418,44 +516,125 @@ bool device_readable(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Launch shape of the persistent solver.  team > 1: the phased plan, all with one block of
+// 1024 threads per SM: first as many full waves of the largest problems as the SMs hold,
+// one block per problem; then the remaining largest problems by clusters of `team` blocks,
+// and everything else one block per problem (team_waves, grid1, grid2 are filled in by
+// plan_phases).
 struct LaunchConfig {
     int threads;       // 256, 512 or 1024
     int blocks_per_sm;
+    int team;          // 1: one phase, one block per problem
+    int first = 0;     // problems (largest first) solved one per block in the first phase
+    int nteam = 0;     // problems after those solved by teams in the second phase
+    int grid1 = 0, grid2 = 0;
 };
 
-rbgs_status launch_persistent(const LaunchConfig &lc, int sms, DevProblem *d_probs, DevResult *d_res,
-                              int *d_order, int nprob, int *d_queue, double tol, int check_every,
-                              long long max_sweeps, int inner, int refine, cudaStream_t s) {
-    RBGS_CUDA(cudaMemsetAsync(d_queue, 0, sizeof(int), s));
-    const int grid = std::max(1, std::min(nprob, sms * lc.blocks_per_sm));
-    switch (lc.threads) {
-    case 256:
-        batched_persistent_kernel<256><<<grid, 256, 0, s>>>(d_probs, d_res, d_order, nprob, d_queue, tol,
-                                                            check_every, max_sweeps, inner, refine);
-        break;
-    case 512:
-        batched_persistent_kernel<512><<<grid, 512, 0, s>>>(d_probs, d_res, d_order, nprob, d_queue, tol,
-                                                            check_every, max_sweeps, inner, refine);
-        break;
-    default:
-        batched_persistent_kernel<1024><<<grid, 1024, 0, s>>>(d_probs, d_res, d_order, nprob, d_queue, tol,
-                                                              check_every, max_sweeps, inner, refine);
-        break;
-    }
-    RBGS_LAUNCH_CHECK();
+template <int THREADS, int CS>
+rbgs_status launch_one(int grid, const DevProblem *d_probs, DevResult *d_res, const int *d_order, int nprob,
+                       int nteam, int *d_queues, double tol, int check_every, long long max_sweeps, int inner,
+                       int refine, int cap_n, cudaStream_t s) {
+    RBGS_CUDA(cudaMemsetAsync(d_queues, 0, 2 * sizeof(int), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = CS > 1 ? 1 : 0;
+    RBGS_CUDA(cudaLaunchKernelEx(&cfg, batched_persistent_kernel<THREADS, CS>, d_probs, d_res, d_order, nprob, nteam,
+                                 d_queues, tol, check_every, max_sweeps, inner, refine, cap_n));
     return RBGS_OK;
 }
 
-// Autotuner: block size and blocks per SM for the persistent kernel.  Neither changes a
-// result bit; each candidate runs a few sweeps of the real batch (after which the
-// problems are re-packed), the fastest per update wins.  Cached per process by
-// (device, precision, sizes).
+// Clusters of CS blocks of 1024 threads that fit on the device at once (0 if none).
+template <int CS>
+int max_clusters() {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS * 64);
+    cfg.blockDim = dim3(1024);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, batched_persistent_kernel<1024, CS>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
+int max_clusters_of(int cs) { return cs == 2 ? max_clusters<2>() : (cs == 4 ? max_clusters<4>() : 0); }
+
+// The phased plan for the problems in order (largest first): m = the problems at the
+// largest size.  Phase one takes floor(m / sms) * sms of them, one block per SM each;
+// phase two gives the remaining ones to clusters of `team` blocks and the rest to single
+// blocks.
+void plan_phases(LaunchConfig &lc, const std::vector<int> &sizes_desc, int sms) {
+    const int nmax = sizes_desc.empty() ? 0 : sizes_desc[0];
+    int m = 0;
+    while (m < (int)sizes_desc.size() && sizes_desc[m] == nmax) ++m;
+    lc.first = (m / sms) * sms;
+    lc.nteam = m - lc.first;
+    lc.grid1 = sms;
+    const int nc = max_clusters_of(lc.team);
+    lc.grid2 = lc.team * std::max(1, nc);
+}
+
+rbgs_status launch_persistent(const LaunchConfig &lc, int sms, const DevProblem *d_probs, DevResult *d_res,
+                              const int *d_order, int nprob, int *d_queues, double tol, int check_every,
+                              long long max_sweeps, int inner, int refine, int cap_n, cudaStream_t s) {
+    if (lc.team > 1) {
+        rbgs_status st = RBGS_OK;
+        if (lc.first > 0)
+            st = launch_one<1024, 1>(lc.grid1, d_probs, d_res, d_order, lc.first, 0, d_queues, tol, check_every,
+                                     max_sweeps, inner, refine, cap_n, s);
+        if (st != RBGS_OK || lc.first >= nprob) return st;
+        const int *rest = d_order + lc.first;
+        const int nrest = nprob - lc.first;
+        if (lc.team == 2)
+            return launch_one<1024, 2>(lc.grid2, d_probs, d_res, rest, nrest, lc.nteam, d_queues, tol, check_every,
+                                       max_sweeps, inner, refine, cap_n, s);
+        return launch_one<1024, 4>(lc.grid2, d_probs, d_res, rest, nrest, lc.nteam, d_queues, tol, check_every,
+                                   max_sweeps, inner, refine, cap_n, s);
+    }
+    const int grid = std::max(1, std::min(nprob, sms * lc.blocks_per_sm));
+    switch (lc.threads) {
+    case 256:
+        return launch_one<256, 1>(grid, d_probs, d_res, d_order, nprob, 0, d_queues, tol, check_every, max_sweeps,
+                                  inner, refine, cap_n, s);
+    case 512:
+        return launch_one<512, 1>(grid, d_probs, d_res, d_order, nprob, 0, d_queues, tol, check_every, max_sweeps,
+                                  inner, refine, cap_n, s);
+    default:
+        return launch_one<1024, 1>(grid, d_probs, d_res, d_order, nprob, 0, d_queues, tol, check_every, max_sweeps,
+                                   inner, refine, cap_n, s);
+    }
+}
+
+// Autotuner: block size and blocks per SM for the persistent kernel, and the phased plan
+// with clusters of 2 or 4 blocks per large problem.  The iterate of every problem is the
+// same under all of them; each candidate runs a probe of the real batch (after which the
+// problems are re-packed), the fastest wins.  Cached per process by (device, precision,
+// team option, sizes).
 struct TuneKey {
-    int device, refine;
+    int device, refine, team;
     std::vector<int> sizes;
-    bool operator==(const TuneKey &o) const { return device == o.device && refine == o.refine && sizes == o.sizes; }
+    bool operator==(const TuneKey &o) const {
+        return device == o.device && refine == o.refine && team == o.team && sizes == o.sizes;
+    }
 };
 std::mutex g_tune_mutex;
+thread_local LaunchConfig g_last_shape{0, 0, 0};
 std::vector<std::pair<TuneKey, LaunchConfig>> g_tune_cache;
 
 }  // namespace
@@ -535,7 +714,7 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
     fail_cuda(cudaMalloc(&d_probs, nprob * sizeof(DevProblem)), "cudaMalloc");
     fail_cuda(cudaMalloc(&d_res, nprob * sizeof(DevResult)), "cudaMalloc");
     fail_cuda(cudaMalloc(&d_order, nprob * sizeof(int)), "cudaMalloc");
-    fail_cuda(cudaMalloc(&d_queue, sizeof(int)), "cudaMalloc");
+    fail_cuda(cudaMalloc(&d_queue, 2 * sizeof(int)), "cudaMalloc");
     if (st == RBGS_OK) fail_cuda(cudaMemsetAsync(pool, 0, total, s), "cudaMemsetAsync");
     for (int p = 0; p < nprob && st == RBGS_OK; ++p) {
         const int n = probs[p].n;
@@ -579,11 +758,26 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
     if (st == RBGS_OK) fail_cuda(cudaMemcpyAsync(d_order, order.data(), nprob * sizeof(int), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync");
     const dim3 pgrid((maxW + 255) / 256, std::min(maxRows, 64), nprob);
 
-    // ---- autotune the launch shape (per process, per device/precision/size mix)
-    LaunchConfig lc{1024, 1};
+    // ---- autotune the launch shape (per process, per device/precision/size mix/team option)
+    std::vector<int> sizes_desc(nprob);
+    for (int q = 0; q < nprob; ++q) sizes_desc[q] = probs[order[q]].n;
+    LaunchConfig lc{1024, 1, 1};
     if (st == RBGS_OK && nprob > 65535) { set_error("at most 65535 problems per batch"); st = RBGS_EINVAL; }
-    if (st == RBGS_OK) {
-        TuneKey key{device, refine, {}};
+    if (st == RBGS_OK && o.team_size != 0 && o.team_size != 1 && o.team_size != 2 && o.team_size != 4) {
+        set_error("team_size must be 0, 1, 2 or 4");
+        st = RBGS_EINVAL;
+    }
+    if (st == RBGS_OK && o.team_size > 1) {
+        // explicit request: the phased plan with clusters of team_size blocks
+        lc = LaunchConfig{1024, 1, o.team_size};
+        if (max_clusters_of(o.team_size) < 1) {
+            set_error("clusters of %d blocks of 1024 threads do not fit on this device", o.team_size);
+            st = RBGS_EINVAL;
+        } else {
+            plan_phases(lc, sizes_desc, sms);
+        }
+    } else if (st == RBGS_OK) {
+        TuneKey key{device, refine, o.team_size, {}};
         for (int p = 0; p < nprob; ++p) key.sizes.push_back(probs[p].n);
         std::sort(key.sizes.begin(), key.sizes.end());
         bool found = false;
@@ -599,21 +793,32 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
             lc.blocks_per_sm = o.tblock_k > 0 ? o.tblock_k : 1;
         }
         if (tune) {
-            const LaunchConfig cands[] = {{1024, 1}, {512, 2}, {512, 1}, {256, 4}, {256, 2}};
+            std::vector<LaunchConfig> cands = {{1024, 1, 1}, {512, 2, 1}, {512, 1, 1}, {256, 4, 1}, {256, 2, 1}};
+            if (o.team_size == 0) {
+                for (int cs : {2, 4}) {
+                    if (max_clusters_of(cs) < 1) continue;
+                    LaunchConfig c{1024, 1, cs};
+                    plan_phases(c, sizes_desc, sms);
+                    cands.push_back(c);
+                }
+            }
             cudaEvent_t e0, e1;
             fail_cuda(cudaEventCreate(&e0), "cudaEventCreate");
             fail_cuda(cudaEventCreate(&e1), "cudaEventCreate");
             float best = 1e30f;
-            const long long probe = refine ? std::min<long long>(inner, 20) : 20;
+            // each probe runs the largest problems `probe` sweeps and a problem of size n
+            // probe * (n / n_max)^2 (at least one), so that its work grows like n^4, as in
+            // a solve to tolerance, and the probe sees the real load balance
+            const long long probe = refine ? std::min<long long>(inner, 32) : 32;
             for (const LaunchConfig &cand : cands) {
                 if (st != RBGS_OK) break;
                 batch_pack_kernel<<<pgrid, 256, 0, s>>>(d_probs);
                 fail_cuda(cudaGetLastError(), "pack launch");
                 fail_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
-                // tol < 0 is never reached: every problem runs exactly `probe` sweeps
+                // tol < 0 is never reached: every problem runs its probe sweeps
                 if (st == RBGS_OK)
                     st = launch_persistent(cand, sms, d_probs, d_res, d_order, nprob, d_queue, -1.0,
-                                           (int)probe, probe, (int)probe, refine, s);
+                                           (int)probe, probe, (int)probe, refine, sizes_desc[0], s);
                 fail_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
                 fail_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
                 float ms = 0.f;
@@ -631,6 +836,7 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
             }
         }
     }
+    g_last_shape = lc;
 
     // ---- the batch: pack -> persistent solve -> unpack, captured as one CUDA graph
     if (st == RBGS_OK) {
@@ -643,7 +849,7 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
             batch_pack_kernel<<<pgrid, 256, 0, cap>>>(d_probs);
             fail_cuda(cudaGetLastError(), "pack launch");
             rbgs_status ls = launch_persistent(lc, sms, d_probs, d_res, d_order, nprob, d_queue, tol,
-                                               o.check_every, o.max_sweeps, inner, refine, cap);
+                                               o.check_every, o.max_sweeps, inner, refine, 0, cap);
             if (ls != RBGS_OK && st == RBGS_OK) st = ls;
             batch_unpack_kernel<<<pgrid, 256, 0, cap>>>(d_probs);
             fail_cuda(cudaGetLastError(), "unpack launch");
@@ -687,4 +893,12 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
     cudaFree(d_order);
     cudaFree(d_queue);
     return first;
+}
+
+extern "C" void rbgs_batched_last_shape(int *threads, int *blocks_per_sm, int *team, int *first, int *nteam) {
+    if (threads) *threads = g_last_shape.threads;
+    if (blocks_per_sm) *blocks_per_sm = g_last_shape.blocks_per_sm;
+    if (team) *team = g_last_shape.team;
+    if (first) *first = g_last_shape.first;
+    if (nteam) *nteam = g_last_shape.nteam;
 }

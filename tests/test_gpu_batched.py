@@ -102,6 +102,66 @@ def test_batched_host_buffers_and_not_converged():
     assert e.value.status == rb.RBGS_ENOTCONV
 
 
+# several problems at the largest size, so that the phased plan gives them to clusters
+TEAM_SIZES = [127, 63, 127, 1, 2, 100, 127, 5, 31, 127, 64, 33]
+
+
+@pytest.mark.parametrize("team", [2, 4])
+def test_batched_teams_match_oracle(team):
+    batch = _batch(TEAM_SIZES, 6)
+    res, outs = _run(batch, 1e-8, check_every=25, team_size=team)
+    shape = rb.rbgs_batched_last_shape()
+    assert shape["team"] == team and shape["first"] == 0 and shape["nteam"] == 4
+    for (n, h2, f, u0), r, got in zip(batch, res, outs):
+        ref = u0.copy()
+        done, rho = oracle.solve(ref, f, h2, 1e-8, 25, 10 ** 7)
+        assert r["status"] == rb.RBGS_OK
+        assert r["sweeps"] == done, (n, r["sweeps"], done)
+        assert abs(r["rel"] - rho) <= 1e-12 * rho
+        _assert_bits(got, ref)
+
+
+@pytest.mark.parametrize("team", [2, 4])
+def test_batched_teams_refinement_matches_oracle(team):
+    batch = _batch([100, 31, 100, 5, 100, 63], 7)
+    res, outs = _run(batch, 1e-9, precision=rb.RBGS_FP32_REFINE, inner_sweeps=40, team_size=team)
+    assert rb.rbgs_batched_last_shape()["nteam"] == 3
+    for (n, h2, f, u0), r, got in zip(batch, res, outs):
+        ref = u0.copy()
+        done, rho, _ = oracle.refine_solve(ref, f, h2, 1e-9, 40, 10 ** 7)
+        assert r["status"] == rb.RBGS_OK and r["sweeps"] == done
+        assert abs(r["rel"] - rho) <= 1e-12 * rho
+        _assert_bits(got, ref)
+
+
+def test_batched_phased_plan_full_wave_then_teams():
+    """More problems at the largest size than SMs: the first phase solves a full wave of
+    them one block per SM, the second gives the rest to clusters of 4 blocks."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sizes = [9] * (sms + 7) + [5, 3, 8]
+    batch = _batch(sizes, 8)
+    res, outs = _run(batch, 1e-8, check_every=10, team_size=4)
+    shape = rb.rbgs_batched_last_shape()
+    assert (shape["team"], shape["first"], shape["nteam"]) == (4, sms, 7)
+    for (n, h2, f, u0), r, got in zip(batch, res, outs):
+        ref = u0.copy()
+        done, rho = oracle.solve(ref, f, h2, 1e-8, 10, 10 ** 7)
+        assert r["status"] == rb.RBGS_OK and r["sweeps"] == done
+        _assert_bits(got, ref)
+
+
+def test_batched_autotuner_reports_its_shape_and_rejects_bad_team():
+    batch = _batch([31, 31, 17], 9)
+    res, outs = _run(batch, 1e-8, check_every=25)
+    shape = rb.rbgs_batched_last_shape()
+    assert shape["team"] in (1, 2, 4) and shape["threads"] in (256, 512, 1024)
+    with pytest.raises(rb.RbgsError) as e:
+        rb.rbgs_solve_batched([(p[0], p[1], p[2], p[3]) for p in batch], 1e-8,
+                              [np.empty((p[0] + 2, p[0] + 2)) for p in batch],
+                              rb.default_opts(team_size=3))
+    assert e.value.status == rb.RBGS_EINVAL
+
+
 @pytest.mark.slow
 def test_batched_512_uneven_problems_sampled():
     """512 problems with the batched workload's recipe (size index and boundary constant
