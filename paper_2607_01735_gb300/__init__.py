@@ -29,7 +29,7 @@ RBGS_KERNEL_AUTO, RBGS_KERNEL_COLOUR, RBGS_KERNEL_TEMPORAL, RBGS_KERNEL_WAVEFRON
 
 # Every symbol include/rbgs.h declares.
 EXPORTED = ("rbgs_default_opts", "rbgs_create", "rbgs_sweep", "rbgs_residual", "rbgs_solve",
-            "rbgs_get_solution", "rbgs_set_solution", "rbgs_solve_batched", "rbgs_destroy",
+            "rbgs_get_solution", "rbgs_set_solution", "rbgs_set_problem", "rbgs_solve_batched", "rbgs_destroy",
             "rbgs_last_error", "rbgs_residual_static", "rbgs_batched_last_shape")
 
 
@@ -88,6 +88,8 @@ def load_library(path: str | None = None):
     lib.rbgs_get_solution.restype = c_int
     lib.rbgs_set_solution.argtypes = [vp, vp]
     lib.rbgs_set_solution.restype = c_int
+    lib.rbgs_set_problem.argtypes = [vp, vp, vp]
+    lib.rbgs_set_problem.restype = c_int
     lib.rbgs_solve_batched.argtypes = [c_int, ctypes.POINTER(Problem), c_double, ctypes.POINTER(Opts),
                                        vp, ctypes.POINTER(vp), ctypes.POINTER(Result)]
     lib.rbgs_solve_batched.restype = c_int
@@ -183,6 +185,10 @@ def rbgs_set_solution(ctx: int, u_in) -> None:
     _check(load_library().rbgs_set_solution(ctx, _ptr(u_in)))
 
 
+def rbgs_set_problem(ctx: int, f, u_init) -> None:
+    _check(load_library().rbgs_set_problem(ctx, _ptr(f), _ptr(u_init)))
+
+
 def rbgs_destroy(ctx: int) -> None:
     if ctx:
         load_library().rbgs_destroy(ctx)
@@ -246,6 +252,9 @@ class Solver:
 
     def set_solution(self, u_in) -> None:
         rbgs_set_solution(self.ctx, u_in)
+
+    def set_problem(self, f, u_init) -> None:
+        rbgs_set_problem(self.ctx, f, u_init)
 
     def close(self) -> None:
         if self.ctx:

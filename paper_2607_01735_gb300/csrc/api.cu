@@ -518,6 +518,12 @@ rbgs_status rbgs_set_solution(rbgs_t c, const double *u_in) {
     return load_problem(c, nullptr, u_in);
 }
 
+rbgs_status rbgs_set_problem(rbgs_t c, const double *f, const double *u_init) {
+    clear_error();
+    if (!c || !f || !u_init) { set_error("ctx, f and u_init must not be NULL"); return RBGS_EINVAL; }
+    return load_problem(c, f, u_init);
+}
+
 void rbgs_destroy(rbgs_t c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);

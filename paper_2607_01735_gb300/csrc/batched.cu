@@ -808,8 +808,10 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
             float best = 1e30f;
             // each probe runs the largest problems `probe` sweeps and a problem of size n
             // probe * (n / n_max)^2 (at least one), so that its work grows like n^4, as in
-            // a solve to tolerance, and the probe sees the real load balance
-            const long long probe = refine ? std::min<long long>(inner, 32) : 32;
+            // a solve to tolerance, and the probe sees the real load balance.  The refined
+            // form probes one whole outer step (FP64 residual, `inner` FP32 sweeps,
+            // correction), the unit its solves repeat.
+            const long long probe = refine ? std::min<long long>(inner, 256) : 32;
             for (const LaunchConfig &cand : cands) {
                 if (st != RBGS_OK) break;
                 batch_pack_kernel<<<pgrid, 256, 0, s>>>(d_probs);

@@ -52,7 +52,7 @@ def test_default_opts(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # rbgs_opts: 3 ints (+4 padding), a long, 7 ints (+4 padding) -> 56 bytes on LP64
+    # rbgs_opts: 3 ints (+4 padding), a long, 8 ints -> 56 bytes on LP64
     assert ctypes.sizeof(rb.Opts) == 56
     assert ctypes.sizeof(rb.Problem) == 32
     assert ctypes.sizeof(rb.Result) == 32
@@ -84,6 +84,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rbgs_residual(None, None) == rb.RBGS_EINVAL
     assert lib.rbgs_solve(None, 1e-8, None, None) == rb.RBGS_EINVAL
     assert lib.rbgs_get_solution(None, None) == rb.RBGS_EINVAL
+    assert lib.rbgs_set_problem(None, None, None) == rb.RBGS_EINVAL
     lib.rbgs_destroy(None)  # ignored
 
 

@@ -252,6 +252,43 @@ def test_set_solution_resumes():
     _assert_bits(out.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("kernel,precision", [(rb.RBGS_KERNEL_COLOUR, rb.RBGS_FP64),
+                                              (rb.RBGS_KERNEL_WAVEFRONT, rb.RBGS_FP64),
+                                              (rb.RBGS_KERNEL_TEMPORAL, rb.RBGS_FP64),
+                                              (rb.RBGS_KERNEL_AUTO, rb.RBGS_FP32_REFINE)])
+@pytest.mark.parametrize("host", [False, True])
+def test_set_problem_reuses_the_context(kernel, precision, host):
+    """A context reloaded with a second problem (host or device inputs) gives the oracle's
+    iterate for that problem, as a freshly created one does; the first problem leaves no
+    trace (graphs, partner buffers and the right-hand side norm are refreshed)."""
+    n = 70
+    h2 = synth.h_squared(n)
+    fa, ua = _problem(n, 83)
+    fb, ub = _problem(n, 84)
+    conv = (lambda a: a) if host else (lambda a: torch.from_numpy(a).cuda())
+    out = np.empty((n + 2, n + 2)) if host else torch.empty(n + 2, n + 2, dtype=torch.float64, device="cuda")
+    refine = precision == rb.RBGS_FP32_REFINE
+    with rb.Solver(n, h2, conv(fa), conv(ua), kernel=kernel, precision=precision, inner_sweeps=10,
+                   max_sweeps=40, check_every=10) as s:
+        for f, u0 in ((fa, ua), (fb, ub)):
+            s.set_problem(conv(f), conv(u0))
+            if refine:
+                _, rho, _ = s.solve(0.0, allow_not_converged=True)
+            else:
+                s.sweep(40)
+                rho = s.residual()
+            s.get_solution(out)
+            got = out if host else out.cpu().numpy()
+            ref = u0.copy()
+            if refine:
+                _, ref_rho, _ = oracle.refine_solve(ref, f, h2, 0.0, 10, 40)
+            else:
+                oracle.sweeps(ref, f, h2, 40)
+                ref_rho = oracle.residual(ref, f, h2)[0]
+            _assert_bits(np.asarray(got), ref)
+            assert abs(rho - ref_rho) <= RESID_RTOL * ref_rho
+
+
 def test_graph_and_direct_launches_agree():
     # 70 sweeps = two cached 32-sweep graphs + 6 direct sweeps
     n = 130
