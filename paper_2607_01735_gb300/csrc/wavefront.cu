@@ -9,7 +9,7 @@
 // The live rows of the iterate (t-2K .. t+3, loaded three steps ahead) sit in a ring of
 // 2K+4 register slots; the step loop is unrolled over the ring so every slot index is a
 // compile-time constant.  The live rows of h2f (t-2K+1 .. t+2) sit in a ring of the same
-// slots in shared memory, filled by cp.async two steps ahead (which frees the registers
+// slots in shared memory, filled by cp.async three steps ahead (which frees the registers
 // for more resident warps).  Rows of the iterate further ahead are prefetched into L1.
 //
 // Decomposition.  A warp owns a strip of 64 values of each colour row (2 per lane) and a
@@ -106,7 +106,7 @@ __device__ __forceinline__ void wf_cp_async(T *dst, const T *src, bool src_valid
 
 __device__ __forceinline__ void wf_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-__device__ __forceinline__ void wf_cp_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
+__device__ __forceinline__ void wf_cp_wait3() { asm volatile("cp.async.wait_group 3;" ::: "memory"); }
 
 __device__ __forceinline__ void wf_prefetch(const void *p) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
@@ -114,7 +114,7 @@ __device__ __forceinline__ void wf_prefetch(const void *p) {
 
 // Ring of WS = 2K + 4 row slots, for the iterate (registers) and h2f (shared memory) alike.  With t_s the first
 // step and rho(i) = i - t_s + 2K, row i lives in slot rho(i) mod WS.  At step t (t - t_s =
-// u mod WS): the iterate's row t+3 is loaded into slot u-1, h2f's row t+2 into slot u-2,
+// u mod WS): the iterate's row t+3 is loaded into slot u-1, h2f's row t+3 into slot u-1,
 // half-sweep h works on row t-h+1 in slot u-3-h (its neighbours in the slots on either
 // side), and row t-2K+1 (slot u+1) is stored.  A slot is refilled only after its row's
 // last use: the iterate's row i is last read at step i+2K, h2f's at step i+2K-1.
@@ -170,13 +170,14 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
             wf_prefetch(p1 + (size_t)r * W + k0);
         }
     };
-    // rows t_s - 2K .. t_s + 2 of the iterate, t_s - 2K + 1 .. t_s + 1 of h2f
+    // rows t_s - 2K .. t_s + 2 of the iterate, t_s - 2K + 1 .. t_s + 2 of h2f
 #pragma unroll
     for (int r = 0; r <= 2 * K + 2; ++r) load2(uw[r], a.u0, a.u1, t_s - 2 * K + r);
 #pragma unroll
-    for (int r = 1; r <= 2 * K + 1; ++r) load_f(r, t_s - 2 * K + r);
+    for (int r = 1; r <= 2 * K + 2; ++r) load_f(r, t_s - 2 * K + r);
     wf_cp_commit();
-    wf_cp_commit();  // two empty groups: the first step's wait then covers the rows above
+    wf_cp_commit();  // three empty groups: the first step's wait then covers the rows above
+    wf_cp_commit();
     wf_cp_commit();
 #pragma unroll
     for (int d = 0; d < kWfPrefetch; ++d) {
@@ -184,24 +185,32 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
     }
 
     // Blocks of WS steps whose rows, loads and stores all lie inside the grid and the
-    // segment, on a strip with no boundary column, run without any of those checks.
+    // segment, on a strip with no boundary column, run without any of those checks: every
+    // lane is inside the grid's columns, and a lane either stores both of its values or
+    // (in the overlap) none.
     const bool full_cols = __all_sync(0xffffffffu, msk0 == (1u << P) - 1 && msk1 == (1u << P) - 1);
+    const bool store_vec = k0 >= olo && k0 + P <= ohi;
     auto run_block = [&](int base, auto fast_tag) {
         constexpr bool FAST = decltype(fast_tag)::value;
 #pragma unroll
         for (int u = 0; u < WS; ++u) {
             const int t = base + u;  // t - t_s = u (mod WS), and t has the parity of u
             if (FAST || t <= t_e) {
-                prefetch2(a.u0, a.u1, t + 3 + kWfPrefetch);
                 if (FAST) {
-                    wf_load(uw[(u + WS - 1) % WS][0], a.u0 + (size_t)(t + 3) * W + k0);
-                    wf_load(uw[(u + WS - 1) % WS][1], a.u1 + (size_t)(t + 3) * W + k0);
+                    const size_t ur = (size_t)(t + 3) * W + k0;
+                    wf_load(uw[(u + WS - 1) % WS][0], a.u0 + ur);
+                    wf_load(uw[(u + WS - 1) % WS][1], a.u1 + ur);
+                    const int fs = (u + WS - 1) % WS;
+                    const size_t fr = (size_t)(t + 3) * W + k0;
+                    wf_cp_async(&fw[fs][0][lane * P], a.hf0 + fr, true);
+                    wf_cp_async(&fw[fs][1][lane * P], a.hf1 + fr, true);
                 } else {
+                    prefetch2(a.u0, a.u1, t + 3 + kWfPrefetch);
                     load2(uw[(u + WS - 1) % WS], a.u0, a.u1, t + 3);
+                    load_f((u + WS - 1) % WS, t + 3);
                 }
-                load_f((u + WS - 2) % WS, t + 2);
                 wf_cp_commit();
-                wf_cp_wait2();  // h2f rows up to t (issued two steps ago) have landed
+                wf_cp_wait3();  // h2f rows up to t (issued three steps ago) have landed
 #pragma unroll
                 for (int h = 1; h <= 2 * K; ++h) {
                     const int i = t - h + 1;
@@ -235,7 +244,13 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
                     }
                 }
                 const int r = t - 2 * K + 1;  // final: every half-sweep has passed it
-                if ((FAST || (r >= row_a && r < row_b)) && kin) {
+                if (FAST) {
+                    if (store_vec) {
+                        const T(&v)[2][P] = uw[(u + 1) % WS];
+                        wf_store(a.o0 + (size_t)r * W + k0, v[0]);
+                        wf_store(a.o1 + (size_t)r * W + k0, v[1]);
+                    }
+                } else if (r >= row_a && r < row_b && kin) {
                     const T(&v)[2][P] = uw[(u + 1) % WS];
                     T *d0 = a.o0 + (size_t)r * W + k0, *d1 = a.o1 + (size_t)r * W + k0;
                     if (k0 >= olo && k0 + P <= ohi) {
