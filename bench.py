@@ -38,6 +38,8 @@ METRIC = "GLUP/s + HBM GB/s vs ~8 TB/s; time-to-residual 1e-8, plain vs chosen f
 UNIT = "GLUP/s"
 BYTES_PER_LUP = 24  # FP64: read h2f and the other colour's value, write the own value
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "half_sweep_f64_n16384.md")
+# side files of a run (nvidia-smi clock samples, trained U-Net parameters)
+OUT_DIR = os.environ.get("RBGS_BENCH_OUT", os.path.join(ROOT, "bench_out"))
 KERNEL_SOURCES = ["paper_2607_01735_gb300/csrc/sweep.cu", "paper_2607_01735_gb300/csrc/sweep_impl.cuh",
                   "paper_2607_01735_gb300/csrc/fp64.cuh"]
 
@@ -157,7 +159,7 @@ class ClockSampler:
     def __init__(self, uuid):
         self.uuid = uuid
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(OUT_DIR, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -654,8 +656,8 @@ def run_learned(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del x, y, m
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    torch.save(net.get_params().cpu(), os.path.join(ROOT, "gpurun_out", "unet_params.pt"))
+    os.makedirs(OUT_DIR, exist_ok=True)
+    torch.save(net.get_params().cpu(), os.path.join(OUT_DIR, "unet_params.pt"))
     results = []
     caps = [int(v) for v in args.eval_cap.split(",")]
     for si, n in enumerate(int(v) for v in args.eval_sizes.split(",")):

@@ -3,8 +3,8 @@
  *
  * The paper has no counterpart: a small convolutional U-Net maps a Poisson problem's
  * right-hand side and Dirichlet data to an initial guess u0 for red-black Gauss-Seidel,
- * which then runs to the same tolerance as from u0 = 0 (so RBGS remains both the
- * fallback and the judge of the network's error).
+ * which then runs to the same tolerance as from u0 = 0 (so RBGS remains the fallback,
+ * and the residual it reaches, not the network, decides the final error).
  *
  * Tensors are NHWC (channels fastest), batch B, height H, width W.  Activations and
  * operands of the convolutions are bfloat16 (uint16_t bit patterns); accumulation is
