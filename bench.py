@@ -37,12 +37,20 @@ sys.path.insert(0, ROOT)
 METRIC = "GLUP/s + HBM GB/s vs ~8 TB/s; time-to-residual 1e-8, plain vs chosen form"
 UNIT = "GLUP/s"
 BYTES_PER_LUP = 24  # FP64: read h2f and the other colour's value, write the own value
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "half_sweep_f64_n16384.md")
+# committed ncu summaries with the DRAM traffic of the FP64 sweep kernels, and the sources
+# each was captured from (the traffic is reported only while they are unchanged)
+PROFILES = {
+    "half_sweep_f64": ("profiles/half_sweep_f64_n16384.md",
+                       ["paper_2607_01735_gb300/csrc/sweep.cu", "paper_2607_01735_gb300/csrc/sweep_impl.cuh",
+                        "paper_2607_01735_gb300/csrc/fp64.cuh"]),
+    "persistent_sweeps<double>": ("profiles/persistent_sweeps_f64_n16384.md",
+                                  ["paper_2607_01735_gb300/csrc/persistent.cu",
+                                   "paper_2607_01735_gb300/csrc/sweep_impl.cuh",
+                                   "paper_2607_01735_gb300/csrc/fp64.cuh"]),
+}
+PERSIST_MIN_N, PERSIST_MAX_N = 416, 1 << 15
 # side files of a run (nvidia-smi clock samples, trained U-Net parameters)
 OUT_DIR = os.environ.get("RBGS_BENCH_OUT", os.path.join(ROOT, "bench_out"))
-KERNEL_SOURCES = ["paper_2607_01735_gb300/csrc/sweep.cu", "paper_2607_01735_gb300/csrc/sweep_impl.cuh",
-                  "paper_2607_01735_gb300/csrc/fp64.cuh"]
-
 
 def parse():
     p = argparse.ArgumentParser()
@@ -99,18 +107,21 @@ def workload(n, sweeps, precision="fp64"):
             f"{sweeps} red+black sweeps + residual norm")
 
 
-def kernel_hash():
+def kernel_hash(sources):
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(emulate):
+def profiled_traffic(kname, emulate):
     """Per-launch DRAM bytes from the committed ncu summary, if it matches this kernel."""
+    if kname not in PROFILES:
+        return None
+    path, sources = PROFILES[kname]
     try:
-        with open(PROFILE_SUMMARY) as fh:
+        with open(os.path.join(ROOT, path)) as fh:
             text = fh.read()
     except OSError:
         return None
@@ -119,7 +130,7 @@ def profiled_traffic(emulate):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_sources_sha256_16") != kernel_hash():
+    if vals.get("kernel_sources_sha256_16") != kernel_hash(sources):
         return None
     if str(vals.get("fp64_emulate")) != str(emulate):
         return None
@@ -127,6 +138,14 @@ def profiled_traffic(emulate):
         return float(vals["traffic_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def uses_persistent(args, n, refine, kernel):
+    """The FP64 sweeps run in one cooperative launch (the library's rule: one launch per
+    colour, or AUTO, with the default launch shape, PERSIST_MIN_N <= n <= PERSIST_MAX_N)."""
+    return (not refine and kernel == 1 and args.tile_rows == 0 and args.emulate in (-1, 0)
+            and args.values in (0, 2) and args.rows in (0, 1) and args.int_rows == 0
+            and PERSIST_MIN_N <= n <= PERSIST_MAX_N)
 
 
 def resolved_kernel(n, refine, kernel, tblock_k):
@@ -769,6 +788,7 @@ def main():
 
     kernel, kdepth = resolved_kernel(n, refine, args.kernel, args.tblock_k)
     blocked = kernel in (2, 3)  # several sweeps per launch (TMA tiles or register wavefront)
+    persistent = uses_persistent(args, n, refine, kernel)
     # pack f, pack u, ||b|| (2), the sweeps, residual (3), unpack
     if refine:
         inner = args.inner or 100
@@ -777,6 +797,8 @@ def main():
         launches_per_step = 4 + 4 + outer * per_outer + 3 + 1
     elif blocked:
         launches_per_step = 4 + sweeps // kdepth + 2 * (sweeps % kdepth) + 3 + 1
+    elif persistent:  # one cooperative launch runs all the sweeps (up to 2^20 per launch)
+        launches_per_step = 4 + -(-sweeps // (1 << 20)) + 3 + 1
     else:
         launches_per_step = 4 + 2 * sweeps + 3 + 1
 
@@ -834,8 +856,10 @@ def main():
         # dominant kernel: the FP64 half-sweep, bound by the FP64 pipe: 4 correctly rounded
         # adds per update (the x0.25 runs on the integer pipe).  Peak: 2 FP64 instructions
         # per clock per SM (ncu's DFMA peak_sustained) x SMs x maximum SM clock.
+        # (the persistent kernel: per half-sweep equivalent, its launch time / (2 sweeps))
         launches = (sweeps // kdepth) if blocked else 2 * sweeps
-        kname = f"{names[kernel]}<double, {kdepth}>" if blocked else "half_sweep_f64"
+        kname = (f"{names[kernel]}<double, {kdepth}>" if blocked
+                 else "persistent_sweeps<double>" if persistent else "half_sweep_f64")
         per_launch_lups = n * n * sweeps / launches
         launch_s = sweep_s / (launches * args.steps)
         fp64_ops = 4 * per_launch_lups
@@ -843,7 +867,7 @@ def main():
         peak_alu = 2.0 * sm_count * sm_mhz * 1e6 / 1e12
         alg_bytes = BYTES_PER_LUP * per_launch_lups
         hbm_achieved = alg_bytes / launch_s / 1e9
-        traffic = None if blocked else profiled_traffic(args.emulate)
+        traffic = None if blocked else profiled_traffic(kname, args.emulate)
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                     "frac": achieved / peak_alu, "traffic": traffic, "kernel": kname,
                     "peak_source": f"FP64 pipe: 2 instr/clk/SM x {sm_count} SMs x {sm_mhz:.0f} MHz "
@@ -851,6 +875,9 @@ def main():
                     "launch_ms": 1e3 * launch_s, "algorithmic_bytes_per_launch": alg_bytes,
                     "hbm": {"achieved": hbm_achieved, "peak": peak_hbm, "unit": "GB/s",
                             "frac": hbm_achieved / peak_hbm, "peak_source": hbm_src}}
+        if persistent:
+            roofline["note"] = ("one cooperative launch runs all sweeps; launch_ms, traffic and the algorithmic "
+                                "bytes are per half-sweep equivalent (the launch / 2 sweeps)")
 
     e2e = None
     if not args.no_e2e:
@@ -918,8 +945,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 f ~ U(-1,1))",
             "config": {"workload": workload(n, sweeps, args.precision), "n": n, "sweeps": sweeps,
-                       "kernel": {1: "one launch per colour", 2: "temporal (TMA tiles)",
-                                  3: "register wavefront"}[kernel],
+                       "kernel": ("all sweeps in one cooperative launch (grid barrier between colours)"
+                                  if persistent else {1: "one launch per colour", 2: "temporal (TMA tiles)",
+                                                      3: "register wavefront"}[kernel]),
                        "tblock_k": kdepth if blocked else None, "precision": args.precision,
                        "fp64_emulate": args.emulate, "tile_rows": args.tile_rows or "auto",
                        "sweep_values": args.values or "auto", "sweep_rows": args.rows or "auto",

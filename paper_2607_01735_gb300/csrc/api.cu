@@ -30,6 +30,19 @@ namespace {
 constexpr int kMaxN = 1 << 18;
 constexpr long kGraphSweeps = 32;    // sweeps per cached graph
 constexpr int kGraphMaxN = 2048;     // graphs pay off where launches dominate
+// FP64 sweeps in one cooperative launch (persistent.cu) for kPersistMinN <= n <= kPersistMaxN.
+// Measured on GB300 against one launch per colour (graphs up to 2048): 0.94x at 383^2,
+// 1.15x at 511^2, 1.29x at 1023^2, 1.32x at 4095^2, 1.10x at 16383^2; below ~400 the grid
+// barrier costs more than a graph's launches.  Above 32768 its flattened item index would
+// leave 32 bits.
+constexpr int kPersistMinN = 416;
+constexpr int kPersistMaxN = 1 << 15;
+
+// One launch per colour requested (or chosen by AUTO) with the default launch shape.
+bool use_persistent(const rbgs_ctx *c) {
+    return c->kernel == RBGS_KERNEL_COLOUR && c->g.n >= kPersistMinN && c->g.n <= kPersistMaxN && c->emulate == 0 &&
+           c->int_rows == 0 && c->pts == 2 && c->sweep_rows == 1 && c->opts.tile_rows == 0;
+}
 
 bool device_accessible(const void *p) {
     cudaPointerAttributes a;
@@ -94,6 +107,7 @@ void free_ctx(rbgs_ctx *c) {
     cudaFree(c->partials);
     cudaFree(c->dsum);
     cudaFree(c->dstatus);
+    cudaFree(c->pcounter);
     if (c->hsum) cudaFreeHost(c->hsum);
     if (c->hstatus) cudaFreeHost(c->hstatus);
     if (c->capture) cudaStreamDestroy(c->capture);
@@ -411,6 +425,7 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     ok = ok && cudaMalloc(&c->partials, 2 * kMaxPartials * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->dsum, 4 * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc(&c->dstatus, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&c->pcounter, sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->hsum, 4 * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->hstatus, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream) == cudaSuccess;
@@ -441,6 +456,7 @@ rbgs_status rbgs_sweep(rbgs_t c, long nsweeps) {
     clear_error();
     if (!c) { set_error("ctx is NULL"); return RBGS_EINVAL; }
     if (nsweeps < 0) { set_error("nsweeps < 0"); return RBGS_EINVAL; }
+    if (use_persistent(c)) return launch_persistent_sweeps<double>(c->f64, nsweeps, c->pcounter, c->dstatus, c->stream);
     if (c->kernel == RBGS_KERNEL_COLOUR && c->g.n <= kGraphMaxN && nsweeps >= kGraphSweeps) {
         rbgs_status st = ensure_graph(c);
         if (st != RBGS_OK) return st;

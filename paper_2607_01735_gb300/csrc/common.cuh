@@ -104,6 +104,7 @@ struct rbgs_ctx {
     int inner_sweeps;           // resolved FP32 sweeps per correction
     int kernel32;               // resolved inner kernel for the FP32 sweeps
     int *hstatus;               // pinned host mirror of dstatus
+    unsigned *pcounter;         // device: grid-barrier counter of the persistent small-grid sweeps
 };
 
 namespace rbgs {
@@ -126,6 +127,11 @@ rbgs_status launch_sweeps_f32(const ColourField<float> &fld, long nsweeps, cudaS
 // one register-wavefront pass of k sweeps from fld.u into fld.alt, then swaps them (wavefront.cu)
 template <typename T>
 rbgs_status launch_wavefront_pass(ColourField<T> &fld, int k, cudaStream_t s);
+// nsweeps FP64 sweeps of fld in cooperative launches with a bounded grid barrier between
+// the colours (persistent.cu); a barrier that gives up sets *status
+template <typename T>
+rbgs_status launch_persistent_sweeps(ColourField<T> &fld, long nsweeps, unsigned *counter, int *status,
+                                     cudaStream_t s);
 // mixed-precision refinement kernels (mixed.cu)
 rbgs_status launch_defect(const rbgs_ctx *c, bool write_r32, double scale, cudaStream_t s);  // -> dsum[0] sum, dsum[2] max
 rbgs_status launch_correct(const rbgs_ctx *c, double scale, cudaStream_t s);
