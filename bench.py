@@ -65,7 +65,9 @@ def parse():
     p.add_argument("--values", type=int, default=0, help="values per thread in a half-sweep (0 auto, 2, 4)")
     p.add_argument("--rows", type=int, default=0, help="rows per loop step in a half-sweep (0 auto, 1, 2)")
     p.add_argument("--int-rows", type=int, default=0, help="hybrid FP64: integer-pipe rows per strip pair")
-    p.add_argument("--kernel", type=int, default=0, help="0 auto, 1 one launch per colour, 2 temporal (TMA tiles), 3 register wavefront")
+    p.add_argument("--kernel", type=int, default=0,
+                   help="0 auto, 1 one launch per colour, 2 temporal (TMA tiles), 3 register wavefront, "
+                        "4 all sweeps in one cooperative launch (FP64)")
     p.add_argument("--tblock-k", type=int, default=0, help="sweeps per temporal or wavefront pass (0 auto)")
     p.add_argument("--precision", choices=["fp64", "refine"], default="fp64",
                    help="fp64: plain FP64 sweeps; refine: FP32 sweeps with FP64 defect correction")
@@ -140,17 +142,22 @@ def profiled_traffic(kname, emulate):
         return None
 
 
-def uses_persistent(args, n, refine, kernel):
-    """The FP64 sweeps run in one cooperative launch (the library's rule: one launch per
-    colour, or AUTO, with the default launch shape, PERSIST_MIN_N <= n <= PERSIST_MAX_N)."""
-    return (not refine and kernel == 1 and args.tile_rows == 0 and args.emulate in (-1, 0)
-            and args.values in (0, 2) and args.rows in (0, 1) and args.int_rows == 0
-            and PERSIST_MIN_N <= n <= PERSIST_MAX_N)
+def uses_persistent(args, n, refine):
+    """The FP64 sweeps run in one cooperative launch: RBGS_KERNEL_PERSISTENT, or AUTO with
+    the default launch shape and PERSIST_MIN_N <= n <= PERSIST_MAX_N (the library's rule)."""
+    if refine:
+        return False
+    if args.kernel == 4:
+        return True
+    return (args.kernel == 0 and args.tile_rows == 0 and args.emulate == -1 and args.values in (0, 2)
+            and args.rows in (0, 1) and args.int_rows <= 0 and PERSIST_MIN_N <= n <= PERSIST_MAX_N)
 
 
 def resolved_kernel(n, refine, kernel, tblock_k):
     """The sweep kernel and depth the library runs (RBGS_KERNEL_AUTO as documented in
     include/rbgs.h): 1 one launch per colour, 2 TMA tiles, 3 register wavefront."""
+    if kernel == 4:  # persistent FP64 sweeps; FP32 inner sweeps as one launch per colour
+        return 1, 1
     if kernel:
         return kernel, (tblock_k or (4 if refine else 2))
     if tblock_k:
@@ -788,7 +795,7 @@ def main():
 
     kernel, kdepth = resolved_kernel(n, refine, args.kernel, args.tblock_k)
     blocked = kernel in (2, 3)  # several sweeps per launch (TMA tiles or register wavefront)
-    persistent = uses_persistent(args, n, refine, kernel)
+    persistent = uses_persistent(args, n, refine)
     # pack f, pack u, ||b|| (2), the sweeps, residual (3), unpack
     if refine:
         inner = args.inner or 100

@@ -54,11 +54,17 @@ typedef enum {
 } rbgs_precision;
 
 typedef enum {
-    RBGS_KERNEL_AUTO = 0,     /* COLOUR, except WAVEFRONT (depth 4) for the FP32 inner
-                                 sweeps of RBGS_FP32_REFINE when n > 2048 and tblock_k = 0 */
+    RBGS_KERNEL_AUTO = 0,     /* FP64 sweeps: PERSISTENT for 416 <= n <= 32768 with the default
+                                 launch-shape options, else COLOUR.  FP32 inner sweeps of
+                                 RBGS_FP32_REFINE: WAVEFRONT (depth 4) when n > 2048 and
+                                 tblock_k = 0, else COLOUR                                   */
     RBGS_KERNEL_COLOUR = 1,   /* one launch per colour (half-sweep kernels)               */
     RBGS_KERNEL_TEMPORAL = 2, /* several sweeps per shared-memory tile, halo recompute      */
-    RBGS_KERNEL_WAVEFRONT = 3 /* several sweeps per pass, a register wavefront per strip   */
+    RBGS_KERNEL_WAVEFRONT = 3,/* several sweeps per pass, a register wavefront per strip   */
+    RBGS_KERNEL_PERSISTENT = 4/* FP64 sweeps: all of an rbgs_sweep call in one cooperative
+                                 launch, a bounded grid barrier between the colours
+                                 (n <= 32768; the launch-shape options do not apply).  FP32
+                                 inner sweeps: as COLOUR                                     */
 } rbgs_kernel;
 
 typedef struct {

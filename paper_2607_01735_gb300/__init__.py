@@ -25,7 +25,7 @@ RBGS_OK, RBGS_EINVAL, RBGS_ENOMEM, RBGS_ECUDA, RBGS_ENOTCONV, RBGS_ENONFINITE, R
 STATUS_NAMES = {0: "RBGS_OK", 1: "RBGS_EINVAL", 2: "RBGS_ENOMEM", 3: "RBGS_ECUDA",
                 4: "RBGS_ENOTCONV", 5: "RBGS_ENONFINITE", 6: "RBGS_ETIMEOUT"}
 RBGS_FP64, RBGS_FP32_REFINE = 0, 1
-RBGS_KERNEL_AUTO, RBGS_KERNEL_COLOUR, RBGS_KERNEL_TEMPORAL, RBGS_KERNEL_WAVEFRONT = 0, 1, 2, 3
+RBGS_KERNEL_AUTO, RBGS_KERNEL_COLOUR, RBGS_KERNEL_TEMPORAL, RBGS_KERNEL_WAVEFRONT, RBGS_KERNEL_PERSISTENT = 0, 1, 2, 3, 4
 
 # Every symbol include/rbgs.h declares.
 EXPORTED = ("rbgs_default_opts", "rbgs_create", "rbgs_sweep", "rbgs_residual", "rbgs_solve",

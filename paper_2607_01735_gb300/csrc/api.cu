@@ -38,11 +38,7 @@ constexpr int kGraphMaxN = 2048;     // graphs pay off where launches dominate
 constexpr int kPersistMinN = 416;
 constexpr int kPersistMaxN = 1 << 15;
 
-// One launch per colour requested (or chosen by AUTO) with the default launch shape.
-bool use_persistent(const rbgs_ctx *c) {
-    return c->kernel == RBGS_KERNEL_COLOUR && c->g.n >= kPersistMinN && c->g.n <= kPersistMaxN && c->emulate == 0 &&
-           c->int_rows == 0 && c->pts == 2 && c->sweep_rows == 1 && c->opts.tile_rows == 0;
-}
+bool use_persistent(const rbgs_ctx *c) { return c->kernel == RBGS_KERNEL_PERSISTENT; }
 
 bool device_accessible(const void *p) {
     cudaPointerAttributes a;
@@ -332,8 +328,11 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     if (o.precision != RBGS_FP64 && o.precision != RBGS_FP32_REFINE) {
         set_error("unknown precision %d", o.precision); return RBGS_EINVAL;
     }
-    if (o.kernel < RBGS_KERNEL_AUTO || o.kernel > RBGS_KERNEL_WAVEFRONT) {
+    if (o.kernel < RBGS_KERNEL_AUTO || o.kernel > RBGS_KERNEL_PERSISTENT) {
         set_error("unknown kernel %d", o.kernel); return RBGS_EINVAL;
+    }
+    if (o.kernel == RBGS_KERNEL_PERSISTENT && n > kPersistMaxN) {
+        set_error("RBGS_KERNEL_PERSISTENT supports n <= %d", kPersistMaxN); return RBGS_EINVAL;
     }
     if (o.fp64_emulate != -1 && !emulation_split_supported(o.fp64_emulate)) {
         set_error("unsupported fp64_emulate %d", o.fp64_emulate); return RBGS_EINVAL;
@@ -374,12 +373,18 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     c->h2 = h2;
     c->opts = o;
     c->stream = (cudaStream_t)cuda_stream;
-    // automatic kernels (measured on GB300): FP64 sweeps run one launch per colour (the
-    // register wavefront reaches the same FP64-pipe limit, with overlap work on top); the
-    // FP32 inner sweeps of the refinement run the register wavefront above 2048^2 (1.6x)
-    // and one launch per colour (with graphs) on smaller grids
+    // automatic kernels (measured on GB300): FP64 sweeps run in one cooperative launch from
+    // 416^2 to 32768^2 with the default launch shape (1.15x at 511^2 to 1.53x at 2047^2 and
+    // 1.10x at 16383^2 over one launch per colour), else one launch per colour with cached
+    // graphs (the register wavefront reaches the same FP64-pipe limit, with overlap work on
+    // top); the FP32 inner sweeps of the refinement run the register wavefront above 2048^2
+    // (1.6x) and one launch per colour (with graphs) on smaller grids
     const bool auto_k = o.kernel == RBGS_KERNEL_AUTO && o.tblock_k == 0;
-    c->kernel = o.kernel == RBGS_KERNEL_AUTO ? RBGS_KERNEL_COLOUR : o.kernel;
+    const bool default_shape = o.fp64_emulate == -1 && o.int_rows <= 0 && (o.sweep_values == 0 || o.sweep_values == 2) &&
+                               (o.sweep_rows == 0 || o.sweep_rows == 1) && o.tile_rows == 0;
+    c->kernel = o.kernel != RBGS_KERNEL_AUTO ? o.kernel
+                : (default_shape && n >= kPersistMinN && n <= kPersistMaxN) ? RBGS_KERNEL_PERSISTENT
+                                                                            : RBGS_KERNEL_COLOUR;
     c->emulate = o.fp64_emulate == -1 ? 0x00 : o.fp64_emulate;
     c->pts = o.sweep_values ? o.sweep_values : 2;
     if (o.tile_rows) {
@@ -406,7 +411,8 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     // than one launch per colour on GB300; the register wavefront faster above 2048^2)
     c->kernel32 = o.kernel == RBGS_KERNEL_AUTO ? ((auto_k && n > 2048) ? RBGS_KERNEL_WAVEFRONT
                                                                        : RBGS_KERNEL_COLOUR)
-                                               : o.kernel;
+                  : o.kernel == RBGS_KERNEL_PERSISTENT ? RBGS_KERNEL_COLOUR
+                                                        : o.kernel;
     c->tblock_k32 = (o.precision == RBGS_FP32_REFINE && o.tblock_k) ? o.tblock_k : 4;
     c->inner_sweeps = o.inner_sweeps ? o.inner_sweeps : 100;
     c->f64.n = n;

@@ -74,12 +74,18 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rbgs_create(4, 0.04, f.ctypes.data, u.ctypes.data, ctypes.byref(bad), None,
                            ctypes.byref(h)) == rb.RBGS_EINVAL
     # kernel choice and the depths each kernel supports
-    for bad in (rb.default_opts(kernel=4), rb.default_opts(kernel=rb.RBGS_KERNEL_WAVEFRONT, tblock_k=3),
+    for bad in (rb.default_opts(kernel=5), rb.default_opts(kernel=rb.RBGS_KERNEL_WAVEFRONT, tblock_k=3),
                 rb.default_opts(kernel=rb.RBGS_KERNEL_WAVEFRONT, tblock_k=1),
                 rb.default_opts(kernel=rb.RBGS_KERNEL_WAVEFRONT, precision=rb.RBGS_FP32_REFINE, tblock_k=8),
                 rb.default_opts(kernel=rb.RBGS_KERNEL_TEMPORAL, tblock_k=6)):
         assert lib.rbgs_create(4, 0.04, f.ctypes.data, u.ctypes.data, ctypes.byref(bad), None,
                                ctypes.byref(h)) == rb.RBGS_EINVAL
+    # the cooperative FP64 launch indexes its items in 32 bits: n <= 32768 (the arrays are
+    # never read: options are checked first)
+    big = rb.default_opts(kernel=rb.RBGS_KERNEL_PERSISTENT)
+    assert lib.rbgs_create(40000, 1e-9, f.ctypes.data, u.ctypes.data, ctypes.byref(big), None,
+                           ctypes.byref(h)) == rb.RBGS_EINVAL
+    assert "32768" in rb.rbgs_last_error()
     assert lib.rbgs_sweep(None, 1) == rb.RBGS_EINVAL
     assert lib.rbgs_residual(None, None) == rb.RBGS_EINVAL
     assert lib.rbgs_solve(None, 1e-8, None, None) == rb.RBGS_EINVAL

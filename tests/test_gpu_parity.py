@@ -79,6 +79,40 @@ def test_bit_exact_against_oracle(n, values, step_rows, int_rows):
     assert abs(rho - rho_ref) <= RESID_RTOL * rho_ref
 
 
+@pytest.mark.parametrize("kernel", [rb.RBGS_KERNEL_COLOUR, rb.RBGS_KERNEL_PERSISTENT])
+@pytest.mark.parametrize("n", SIZES)
+def test_explicit_kernel_bit_exact(n, kernel):
+    """One launch per colour and the cooperative launch on every size, whichever AUTO would
+    pick there (it picks the cooperative launch from 416^2)."""
+    f, u0 = _problem(n, 17 + n)
+    h2 = synth.h_squared(n)
+    sweeps = 7 if n > 300 else 13
+    got, rho = _run_gpu(n, h2, f, u0, sweeps, kernel=kernel)
+    ref = u0.copy()
+    oracle.sweeps(ref, f, h2, sweeps)
+    _assert_bits(got, ref)
+    rho_ref = oracle.residual(ref, f, h2)[0]
+    assert abs(rho - rho_ref) <= RESID_RTOL * rho_ref
+
+
+def test_cooperative_launch_in_solve_chunks():
+    """rbgs_solve through the cooperative launch: one launch per check interval, the same
+    sweep count and iterate as the oracle's solve."""
+    n = 600
+    f, u0 = _problem(n, 91, interior=False)
+    h2 = synth.h_squared(n)
+    fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u0).cuda()
+    out = torch.empty_like(ud)
+    with rb.Solver(n, h2, fd, ud, kernel=rb.RBGS_KERNEL_PERSISTENT, check_every=37, max_sweeps=400) as s:
+        done, rho, _ = s.solve(1e-30, allow_not_converged=True)
+        s.get_solution(out)
+    ref = u0.copy()
+    ref_done, ref_rho = oracle.solve(ref, f, h2, 1e-30, 37, 400)
+    assert done == ref_done == 400
+    _assert_bits(out.cpu().numpy(), ref)
+    assert abs(rho - ref_rho) <= RESID_RTOL * ref_rho
+
+
 @pytest.mark.parametrize("values", [2, 4])
 @pytest.mark.parametrize("emulate", [-2, 0x00, 0x08, 0x88, 0x8C, 0xCC, 0xFF])
 @pytest.mark.parametrize("n", [33, 257])
