@@ -10,9 +10,9 @@ i.i.d. from counter stream 1, u0 = 0, h = 1/16385.
 
 `value` is whole-job GLUP/s (lattice-site updates, N^2 per sweep) with the inputs
 resident in device memory; `e2e` is the same step with the inputs and the solution in
-pinned host memory (copies inside the timed region), two contexts on two streams so
-that one step's copies overlap the other's sweeps (`e2e.serial`: one context, nothing
-overlapped).  With N > 1 processes (torchrun) every rank solves its own replica (the
+pinned host memory (copies inside the timed region), the copies of one step overlapping
+the neighbouring steps' sweeps as a serving loop runs them (`e2e.serial`: host buffers
+passed to the library, nothing overlapped).  With N > 1 processes (torchrun) every rank solves its own replica (the
 single-grid path does not shard here) and the value is the sum over ranks over the
 slowest rank's time.
 
@@ -771,6 +771,9 @@ def main():
     # the residual and reads the solution back.
     def start(ctx, fi, ui, cuda_stream, record=False):
         rb.rbgs_set_problem(ctx, fi, ui)
+        run_sweeps(ctx, cuda_stream, record)
+
+    def run_sweeps(ctx, cuda_stream, record=False):
         if record:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(cuda_stream)
@@ -888,35 +891,57 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        # End to end from pinned host memory: each step copies its f and u0 in, solves and
-        # copies the solution and rho out.  Two contexts on two streams alternate, so one
-        # step's copies overlap the other step's sweeps (a stream of solves, as a serving
-        # loop runs them); the serial figure (one context, nothing overlapped) is beside it.
+        # End to end from pinned host memory: every step copies its f and u0 in from pinned
+        # host buffers, solves, and copies the solution and rho out.  As a serving loop runs
+        # a stream of solves, the copies go on a copy stream into device buffers (double
+        # buffered) while the previous or next step's sweeps run; the library then loads from
+        # and unpacks to device memory.  The serial figure beside it passes the host buffers
+        # to the library directly, one step after another, nothing overlapped.
         fh = f.cpu().pin_memory()
         uh = u0.cpu().pin_memory()
         oh = torch.empty(n + 2, n + 2, dtype=torch.float64).pin_memory()
-        stream_b = torch.cuda.Stream(dev)
-        ctx_b = rb.rbgs_create(n, h2, fh, uh, opts, stream=stream_b.cuda_stream)
-        ctxs = ((ctx_a, stream), (ctx_b, stream_b))
+        copy_stream = torch.cuda.Stream(dev)
+        d_in = [(torch.empty_like(f), torch.empty_like(u0)) for _ in range(2)]
+        d_out = [torch.empty_like(u0) for _ in range(2)]
 
         def pipelined(k):
-            pending = None
+            ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+            ev_out = [None, None]
+            with torch.cuda.stream(copy_stream):
+                d_in[0][0].copy_(fh, non_blocking=True)
+                d_in[0][1].copy_(uh, non_blocking=True)
+                ev_in[0].record(copy_stream)
             for i in range(k):
-                c, cs = ctxs[i % 2]
-                start(c, fh, uh, cs)
-                if pending is not None:
-                    finish(pending, oh)
-                pending = c
-            finish(pending, oh)
+                b = i % 2
+                stream.wait_event(ev_in[b])
+                rb.rbgs_set_problem(ctx_a, d_in[b][0], d_in[b][1])
+                if i + 1 < k:  # the next step's inputs, during this step's sweeps
+                    nb = 1 - b
+                    with torch.cuda.stream(copy_stream):
+                        d_in[nb][0].copy_(fh, non_blocking=True)
+                        d_in[nb][1].copy_(uh, non_blocking=True)
+                        ev_in[nb].record(copy_stream)
+                run_sweeps(ctx_a, stream)
+                rb.rbgs_residual(ctx_a)
+                if ev_out[b] is not None:
+                    stream.wait_event(ev_out[b])  # d_out[b]'s previous copy-out has finished
+                rb.rbgs_get_solution(ctx_a, d_out[b])
+                ready = torch.cuda.Event()
+                ready.record(stream)
+                with torch.cuda.stream(copy_stream):
+                    copy_stream.wait_event(ready)
+                    oh.copy_(d_out[b], non_blocking=True)  # during the next step's sweeps
+                    ev_out[b] = torch.cuda.Event()
+                    ev_out[b].record(copy_stream)
 
         def timed(body):
             with ClockSampler(str(uuid) if uuid else None) as clk:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                stream_b.wait_event(e0)
+                copy_stream.wait_event(e0)
                 body()
                 j = torch.cuda.Event()
-                j.record(stream_b)
+                j.record(copy_stream)
                 stream.wait_event(j)
                 e1.record(stream)
                 barrier()
@@ -927,16 +952,17 @@ def main():
                 et = float(tt.item())
             return et, clk.summary()
 
-        pipelined(2)  # warm the host path and the second context
+        pipelined(2)  # warm the host path
+        step(fh, uh, oh)
         barrier()
         et, e2e_clocks = timed(lambda: pipelined(args.steps))
         et_serial, _ = timed(lambda: [step(fh, uh, oh) for _ in range(args.steps)])
-        rb.rbgs_destroy(ctx_b)
         e2e = {"value": lups / et / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 8 * (n * n + (n + 2) * (n + 2)),
                "d2h_bytes_per_step": 8 * (n + 2) * (n + 2) + 8,
                "ms_per_step": 1e3 * et / args.steps, "clocks": e2e_clocks,
-               "pipelined": "two contexts on two streams: a step's host copies overlap the other's sweeps",
+               "pipelined": "host copies on a copy stream into double-buffered device inputs and out of "
+                            "the device solution, overlapping the neighbouring steps' sweeps",
                "serial": {"value": lups / et_serial / 1e9, "ms_per_step": 1e3 * et_serial / args.steps}}
     rb.rbgs_destroy(ctx_a)
 
