@@ -45,6 +45,7 @@ PROFILES = {
                         "paper_2607_01735_gb300/csrc/fp64.cuh"]),
     "persistent_sweeps<double>": ("profiles/persistent_sweeps_f64_n16384.md",
                                   ["paper_2607_01735_gb300/csrc/persistent.cu",
+                                   "paper_2607_01735_gb300/csrc/grid_barrier.cuh",
                                    "paper_2607_01735_gb300/csrc/sweep_impl.cuh",
                                    "paper_2607_01735_gb300/csrc/fp64.cuh"]),
 }

@@ -15,13 +15,13 @@
 // was written by other blocks during this launch.  The update is the library's, step by
 // step correctly rounded, so the iterate is bit-identical to one launch per colour.
 //
-// Grid barrier: one counter per launch, zeroed before it.  A block's thread 0 fences its
-// block's writes, adds one, and polls (acquire) until the counter reaches the number of
-// blocks times the barriers passed.  Every wait is bounded: after kBarrierPolls polls, or
-// as soon as another block has given up, the block records a status and leaves; the host
-// reports it as RBGS_ETIMEOUT at its next synchronising call.
+// Grid barrier (grid_barrier.cuh): one counter per launch, zeroed before it.  Every wait is
+// bounded: after kBarrierPolls polls, or as soon as another block has given up, the block
+// records a status and leaves; the host reports it as RBGS_ETIMEOUT at its next
+// synchronising call.
 #include "common.cuh"
 #include "fp64.cuh"
+#include "grid_barrier.cuh"
 #include "sweep_impl.cuh"
 
 namespace rbgs {
@@ -41,33 +41,6 @@ struct PArgs {
     int *status;
     double one;  // 1.0 at run time: the FP64 adds stay fused multiply-adds with it
 };
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Returns false when the barrier gave up (this block's or another block's wait ran out).
-__device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target, int *status) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();  // the block's stores of this phase, before its arrival
-        atomicAdd(counter, 1u);
-        int ok = 1;
-        for (uint32_t q = 0; ld_acquire_gpu(counter) < target; ++q) {
-            if (q >= kBarrierPolls || *reinterpret_cast<volatile int *>(status) != 0) {
-                ok = 0;
-                break;
-            }
-        }
-        if (!ok) atomicOr(status, 2);
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 __device__ __forceinline__ double upd(double hf, double vn, double vs, double vw, double ve, double one) {
     return update_f64<false>(0, hf, vn, vs, vw, ve, one);
@@ -125,10 +98,10 @@ __global__ void __launch_bounds__(kPThreads) persistent_sweeps(const PArgs<T> a)
     for (long long s = 0; s < a.nsweeps; ++s) {
         half_sweep<T, 0>(a);
         target += gridDim.x;
-        if (!grid_barrier(a.counter, target, a.status)) return;
+        if (!grid_barrier(a.counter, target, a.status, kBarrierPolls)) return;
         half_sweep<T, 1>(a);
         target += gridDim.x;
-        if (!grid_barrier(a.counter, target, a.status)) return;
+        if (!grid_barrier(a.counter, target, a.status, kBarrierPolls)) return;
     }
 }
 

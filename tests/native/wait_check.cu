@@ -2,12 +2,16 @@
 //  * csrc/tma.cuh: one kernel waits on a barrier that nothing completes and must give up
 //    after `polls` polls and report it; a control kernel arrives on the barrier first
 //    and must see it complete.
+//  * csrc/grid_barrier.cuh (the cooperative FP64 sweep launch): two blocks of a cooperative
+//    launch meet at the barrier; with one block absent (it leaves at once), the other's wait
+//    must run out after `polls` polls and set the status instead of waiting forever.
 //  * csrc/conv_wait.cuh (the convolution kernels' abort protocol): one role spins on a
 //    barrier that nothing completes, another role waits (suspending) on a second barrier
 //    that nothing completes either.  The side with the short limit must give up and raise
 //    the abort flag; the other must leave through the flag, long before its own limit.
 // Test infrastructure only.
 #include "../../paper_2607_01735_gb300/csrc/conv_wait.cuh"
+#include "../../paper_2607_01735_gb300/csrc/grid_barrier.cuh"
 #include "../../paper_2607_01735_gb300/csrc/tma.cuh"
 
 namespace {
@@ -49,7 +53,35 @@ __global__ void abort_kernel(unsigned polls, unsigned waiter_polls, int *status,
     }
 }
 
+__global__ void grid_barrier_kernel(unsigned *counter, int *status, int absent, unsigned polls, int *passed) {
+    if (absent && blockIdx.x == 1) return;  // this block never arrives
+    const bool ok = rbgs::grid_barrier(counter, gridDim.x, status, polls);
+    if (ok && threadIdx.x == 0) atomicAdd(passed, 1);
+}
+
 }  // namespace
+
+// out_host[0]: the status word, out_host[1]: blocks that passed the barrier.
+extern "C" int run_grid_barrier_check(int absent, unsigned polls, int *out_host) {
+    unsigned *counter = nullptr;
+    int *d = nullptr;
+    if (cudaMalloc(&counter, sizeof(unsigned)) != cudaSuccess) return 1;
+    if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) {
+        cudaFree(counter);
+        return 1;
+    }
+    cudaMemset(counter, 0, sizeof(unsigned));
+    cudaMemset(d, 0, 2 * sizeof(int));
+    int *status = d, *passed = d + 1;
+    void *args[] = {&counter, &status, &absent, &polls, &passed};
+    cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(grid_barrier_kernel), dim3(2),
+                                                dim3(64), args, 0, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, d, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(counter);
+    cudaFree(d);
+    return e == cudaSuccess ? 0 : 2;
+}
 
 extern "C" int run_abort_check(unsigned polls, unsigned waiter_polls, int *out_host) {
     int *d = nullptr;

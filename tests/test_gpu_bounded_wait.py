@@ -3,6 +3,8 @@
 * The bounded mbarrier wait that guards the temporally blocked kernel's TMA loads gives up
   on a barrier nothing completes, reports it through a status word, and the context stays
   usable (a control wait then completes).
+* The grid barrier of the cooperative FP64 sweep launch: a block whose partner never
+  arrives gives up after its poll limit and reports it; with both blocks present, both pass.
 * The convolution kernels' abort protocol: a role whose wait runs out raises the block's
   abort flag and the failure word, and a role waiting on a hand-off from it leaves through
   the flag instead of waiting out its own (much longer) limit."""
@@ -32,6 +34,8 @@ def lib():
     l.run_wait_check.argtypes = [ctypes.c_uint, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     l.run_wait_check.restype = ctypes.c_int
     l.run_abort_check.argtypes = [ctypes.c_uint, ctypes.c_uint, ctypes.POINTER(ctypes.c_int)]
+    l.run_grid_barrier_check.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.POINTER(ctypes.c_int)]
+    l.run_grid_barrier_check.restype = ctypes.c_int
     l.run_abort_check.restype = ctypes.c_int
     return l
 
@@ -59,3 +63,12 @@ def test_abort_flag_releases_the_other_roles(lib, issuer_polls, waiter_polls, wh
         assert (fail_issuer, fail_waiter) == (1, 0)
     else:
         assert (fail_issuer, fail_waiter) == (0, 1)
+
+
+def test_grid_barrier_gives_up_when_a_block_never_arrives(lib):
+    out = (ctypes.c_int * 2)()
+    assert lib.run_grid_barrier_check(1, 1000, out) == 0
+    assert (out[0], out[1]) == (2, 0)  # the waiting block gave up and said so
+    out = (ctypes.c_int * 2)()
+    assert lib.run_grid_barrier_check(0, 1 << 20, out) == 0
+    assert (out[0], out[1]) == (0, 2)  # both present: both pass, no status
