@@ -378,3 +378,35 @@ def test_full_size_16384_sampled():
     f_host = fd.cpu().numpy()
     rho_ref = oracle.residual(host, f_host, h2)[0]
     assert abs(rho - rho_ref) <= RESID_RTOL * rho_ref
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n", [32768, 32769])
+def test_largest_cooperative_size_and_the_one_past_it(n):
+    """AUTO runs the cooperative launch up to n = 32768, where its flattened item index
+    reaches 32768 * 16385 items, and one launch per colour from 32769 on.  Both sizes are
+    checked on sampled points (oracle windows, corners and the last rows included) and on
+    the residual of the final iterate."""
+    sweeps, stream = 3, 5
+    h2 = synth.h_squared(n)
+    fd = synth.uniform_pm1_grid(n, stream, device="cuda")
+    ud = torch.zeros(n + 2, n + 2, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(ud)
+    with rb.Solver(n, h2, fd, ud) as s:
+        s.sweep(sweeps)
+        s.get_solution(out)
+        rho = s.residual()
+    del ud
+    r = 2 * sweeps + 1
+    samples = [(1, 1), (1, n), (n, 1), (n, n), (n - 1, n - 2), (n // 2, n // 2 + 1), (32000, 30001), (2, n - 1)]
+    for (i, j) in samples:
+        a, c, fw = _window_inputs(n, stream, i, j, r)
+        uw = np.zeros((fw.shape[0] + 2, fw.shape[1] + 2))
+        oracle.sweeps(uw, fw, h2, sweeps, (a - 1 + c - 1) & 1)
+        assert float(out[i, j].item()) == uw[i - a + 1, j - c + 1], (i, j)
+    host = out.cpu().numpy()
+    del out
+    f_host = fd.cpu().numpy()
+    del fd
+    rho_ref = oracle.residual(host, f_host, h2)[0]
+    assert abs(rho - rho_ref) <= RESID_RTOL * rho_ref
