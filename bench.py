@@ -168,6 +168,19 @@ def resolved_kernel(n, refine, kernel, tblock_k):
     return 1, 1
 
 
+def device_peaks(dev):
+    """(FP64-pipe peak in T adds/s with its source, HBM GB/s with its source) for `dev`."""
+    import torch
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0)) if peaks else 2070.0
+    alu = 2.0 * sms * mhz * 1e6 / 1e12
+    alu_src = f"FP64 pipe: 2 instr/clk/SM x {sms} SMs x {mhz:.0f} MHz (one flop = one correctly rounded FP64 add)"
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+    return alu, alu_src, hbm, hbm_src
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -419,6 +432,21 @@ def run_batched(args):
                 "glups": lups / t / 1e9, "total_sweeps": int(sum(r["sweeps"] for r in allres.values())),
                 "launch_shape": rb.rbgs_batched_last_shape(),
                 "step_s": [round(x, 4) for x in times]}
+        alu, alu_src, hbm, hbm_src = device_peaks(dev)
+        if refine:  # FP32 sweeps dominate; the problems are L2-resident, so this is a floor
+            achieved = 12.0 * lups / t / 1e9
+            line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm * world, "unit": "GB/s",
+                                "frac": achieved / (hbm * world), "traffic": None,
+                                "kernel": "batched_persistent_kernel (FP32 inner sweeps)", "peak_source": hbm_src,
+                                "note": "algorithmic FP32 sweep bytes (12 B per update) over the batch time; "
+                                        "the problems are L2-resident"}
+        else:
+            achieved = 4.0 * lups / t / 1e12
+            line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": alu * world, "unit": "TFLOP/s",
+                                "frac": achieved / (alu * world), "traffic": None,
+                                "kernel": "batched_persistent_kernel (FP64 sweeps)", "peak_source": alu_src,
+                                "note": "4 FP64 adds per update of every problem over the batch time, "
+                                        "residual checks and load imbalance included"}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -495,6 +523,17 @@ def run_mixed(args):
                        "extrapolation": "measured cost per sweep x sweeps needed at the asymptotic "
                                         "rate cos^2(pi h) after the measured sweeps"},
             "speedup_vs_plain_fp64": p_est / r_est, "forms": forms, "clocks": clocks.summary()}
+    alu, alu_src, hbm, hbm_src = device_peaks(dev)
+    r_bytes = 3.0 * 1e9 * forms["fp32_refine"]["glups"] / 1e9  # 12 B per point per 4-sweep pass
+    line["roofline"] = {"bound": "hbm", "achieved": r_bytes, "peak": hbm, "unit": "GB/s", "frac": r_bytes / hbm,
+                        "traffic": None, "kernel": "wavefront_kernel<float, 4> (the refined form's inner sweeps)",
+                        "peak_source": hbm_src,
+                        "note": "algorithmic bytes of the FP32 passes (3 B per update) over the refined form's "
+                                "whole time, FP64 defect and correction included",
+                        "plain_fp64": {"bound": "alu", "achieved": 4.0 * forms["plain_fp64"]["glups"] / 1e3,
+                                       "peak": alu, "unit": "TFLOP/s",
+                                       "frac": 4.0 * forms["plain_fp64"]["glups"] / 1e3 / alu,
+                                       "peak_source": alu_src}}
     print(json.dumps(line))
     return 0
 
