@@ -36,6 +36,10 @@ constexpr int kGraphMaxN = 2048;     // graphs pay off where launches dominate
 // barrier costs more than a graph's launches.  Above 32768 its flattened item index would
 // leave 32 bits.
 constexpr int kPersistMinN = 416;
+// FP32 inner sweeps in one launch of one 16-block cluster (cluster_sweeps.cu) up to this
+// size.  Measured on GB300 against cached graphs of one launch per colour: 1.42x at 63^2,
+// 1.46x at 127^2, 0.93x at 255^2, 0.49x at 511^2 (16 SMs do not match the whole GPU there).
+constexpr int kClusterMaxN = 160;
 constexpr int kPersistMaxN = 1 << 15;
 
 bool use_persistent(const rbgs_ctx *c) { return c->kernel == RBGS_KERNEL_PERSISTENT; }
@@ -217,6 +221,10 @@ rbgs_status defect_stats(rbgs_ctx *c, double *rho, double *mx) {
 }
 
 rbgs_status inner_sweeps_f32(rbgs_ctx *c, long m) {
+    // small grids: all m sweeps in one launch of one thread-block cluster
+    if (c->kernel32 == RBGS_KERNEL_COLOUR && c->opts.tile_rows == 0 && c->g.n <= kClusterMaxN &&
+        cluster_sweeps_f32_fit(c->g.n, c->f32.W))
+        return launch_cluster_sweeps_f32(c->f32, m, c->stream);
     // full inner blocks of one-launch-per-colour sweeps on small grids: a cached graph
     if (c->kernel32 == RBGS_KERNEL_COLOUR && m == c->inner_sweeps && c->g.n <= kGraphMaxN) {
         if (!c->graph32) {

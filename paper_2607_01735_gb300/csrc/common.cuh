@@ -132,6 +132,10 @@ rbgs_status launch_wavefront_pass(ColourField<T> &fld, int k, cudaStream_t s);
 template <typename T>
 rbgs_status launch_persistent_sweeps(ColourField<T> &fld, long nsweeps, unsigned *counter, int *status,
                                      cudaStream_t s);
+// FP32 inner sweeps in one launch of one thread-block cluster, d held in its shared memory
+// (cluster_sweeps.cu); usable when d of an n^2 grid with row pitch W fits the cluster
+bool cluster_sweeps_f32_fit(int n, int W);
+rbgs_status launch_cluster_sweeps_f32(ColourField<float> &fld, long nsweeps, cudaStream_t s);
 // mixed-precision refinement kernels (mixed.cu)
 rbgs_status launch_defect(const rbgs_ctx *c, bool write_r32, double scale, cudaStream_t s);  // -> dsum[0] sum, dsum[2] max
 rbgs_status launch_correct(const rbgs_ctx *c, double scale, cudaStream_t s);

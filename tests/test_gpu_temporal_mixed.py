@@ -83,6 +83,27 @@ def test_temporal_fp64_solve_and_resume():
     _assert_bits(out.cpu().numpy(), ref)
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 16, 17, 64, 160, 161])
+def test_refinement_small_grids_bit_exact(n):
+    """Small grids run the FP32 inner sweeps in one launch of one thread-block cluster (up to
+    160^2; most blocks hold one row or none at the smallest sizes), 161^2 the cached graphs."""
+    f, u0 = _problem(n, 700 + n, interior=False)
+    h2 = synth.h_squared(n)
+    inner, max_sweeps = 17, 17 * 2 + 3
+    ref = u0.copy()
+    done_ref, rho_ref, outer = oracle.refine_solve(ref, f, h2, 1e-30, inner, max_sweeps)
+    fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u0).cuda()
+    out = torch.empty_like(ud)
+    with rb.Solver(n, h2, fd, ud, precision=rb.RBGS_FP32_REFINE, inner_sweeps=inner,
+                   max_sweeps=max_sweeps) as s:
+        done, rho, st = s.solve(1e-30, allow_not_converged=True)
+        s.get_solution(out)
+    # (the tiniest grids may reach rho = 0 before max_sweeps; the oracle then stops too)
+    assert done == done_ref
+    _assert_bits(out.cpu().numpy(), ref)
+    assert abs(rho - rho_ref) <= 1e-12 * max(rho_ref, 1e-300) or rho == rho_ref
+
+
 @pytest.mark.parametrize("kernel,k", [(rb.RBGS_KERNEL_COLOUR, 0), (rb.RBGS_KERNEL_TEMPORAL, 2),
                                       (rb.RBGS_KERNEL_TEMPORAL, 4), (rb.RBGS_KERNEL_TEMPORAL, 8)])
 @pytest.mark.parametrize("n", [33, 150, 520])
