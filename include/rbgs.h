@@ -12,8 +12,10 @@
  *   (i + j odd); one red+black pair is one sweep (Algorithms 1 and 2).
  *
  * Arithmetic: every update is evaluated as (((h2*f + N) + S) + W) + E, times 0.25, with
- * each operation correctly rounded and no fused multiply-add, so the FP64 path gives
- * the same bits as a plain sequential C loop in that order.
+ * each operation correctly rounded and h2*f never contracted into an add (h2*f is formed
+ * once, when a problem is loaded).  The FP64 adds run as fused multiply-adds by 1.0, which
+ * round the exact sum once, the same value as the add; x0.25 is an exact exponent step.
+ * So the FP64 path gives the same bits as a plain sequential C loop in that order.
  *
  * Grids, all row-major, i = row (x, slow), j = column (y, fast):
  *   f      N x N interior values (f_ij at index (i-1)*N + (j-1)), float64
@@ -45,7 +47,9 @@ typedef enum {
     RBGS_ECUDA = 3,       /* a CUDA runtime/driver call failed                           */
     RBGS_ENOTCONV = 4,    /* rbgs_solve reached max_sweeps; the iterate is kept          */
     RBGS_ENONFINITE = 5,  /* the residual became NaN or Inf                              */
-    RBGS_ETIMEOUT = 6     /* a bounded device-side wait gave up (batched solver)         */
+    RBGS_ETIMEOUT = 6     /* a bounded device-side wait gave up: the grid barrier of the
+                             cooperative FP64 launch or the TMA wait of the temporal
+                             kernel (reported at the next synchronising call)             */
 } rbgs_status;
 
 typedef enum {
