@@ -1,20 +1,23 @@
-// Batched solve of many independent Poisson problems of uneven sizes in one persistent
-// launch (rbgs_solve_batched).
+// Batched solve of many independent Poisson problems of uneven sizes in persistent launches
+// (rbgs_solve_batched).
 //
 // Design.  The problems are independent, so the batch shards by problem with no data
-// exchange.  A persistent grid of thread blocks (a few per SM) pulls problem indices,
-// largest first, from an atomic work counter; the block that claims a problem solves
-// it to tolerance on its own: red half-sweep, __syncthreads, black half-sweep,
-// __syncthreads (the colour phases of Algorithm 1 at block scope), a deterministic
-// block reduction of the residual every `check_every` sweeps (FP64), or the
-// mixed-precision refinement loop (FP64 defect/correction, FP32 sweeps).  No block ever
-// waits on another block, so there is nothing that can deadlock or spin.  Each problem
-// records %globaltimer stamps when its block starts and finishes it.
+// exchange.  A persistent grid of thread blocks pulls problem indices, largest first, from
+// an atomic work counter; a team that claims a problem solves it to tolerance on its own:
+// red half-sweep, team barrier, black half-sweep, team barrier (the colour phases of
+// Algorithm 1), a deterministic reduction of the residual every `check_every` sweeps
+// (FP64), or the mixed-precision refinement loop (FP64 defect/correction, FP32 sweeps).
+// A team is one block, or the blocks of one thread-block cluster for the largest problems
+// left over after full waves (the phased plan: a launch of full waves, one block per
+// problem, then a launch in which clusters take the leftover largest problems and single
+// blocks the rest).  No block waits on a block outside its cluster; a cluster's blocks
+// reach the same barriers on every path.  Each problem records %globaltimer stamps when
+// its team starts and finishes it.
 //
 // The arithmetic per update is the one of the single-problem kernels (same operations,
 // same order), so every problem's iterate equals the oracle's after the same sweeps.
 // The host side packs all problems into one device pool (colour-split layout), captures
-// pack -> persistent kernel -> unpack into a CUDA graph and launches it.
+// pack -> persistent launches -> unpack into a CUDA graph and launches it.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
