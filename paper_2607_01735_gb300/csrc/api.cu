@@ -1,7 +1,8 @@
 // C ABI entry points of librbgs (declared in include/rbgs.h): context life cycle,
-// layout staging, sweep scheduling (direct launches, a cached CUDA graph, or temporally
-// blocked passes), residual evaluation, the convergence loop and the mixed-precision
-// refinement loop.
+// layout staging, sweep scheduling (one cooperative launch for all sweeps, direct
+// launches, a cached CUDA graph, temporally blocked passes, or one cluster launch for the
+// FP32 inner sweeps of small grids), residual evaluation, the convergence loop and the
+// mixed-precision refinement loop.
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
