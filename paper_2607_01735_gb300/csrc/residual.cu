@@ -7,12 +7,19 @@
 // then the block, then one partial per block; a single-block kernel adds the partials
 // in a fixed order.  The result is the same on every run.
 //
+// The adds run as fused multiply-adds by a run-time 1.0 (one rounding of the exact sum,
+// the same value as the add, on GB300's faster-issuing DFMA path), and rt as
+// fma(-4, u, s), the same value as s + (-4u) because 4u is exact.  GB300's FP64 pipe, not
+// HBM, bounds this walk.
+//
 // ||h^2 b|| depends only on f and the ring; it is reduced once per problem by
-// rhs_norm_kernel (h2f plus the ring neighbours of each boundary-adjacent point).
+// rhs_norm_kernel (h2f plus the ring neighbours of each boundary-adjacent point), walking
+// the colour rows without any index division.
 //
 // The same walk also serves the mixed-precision refinement: max |rt| (exact, order-
 // independent) and the FP32 scaled defect (float)(rt * 2^-e) for the inner solver.
 #include "common.cuh"
+#include "fp64.cuh"
 #include "sweep_impl.cuh"
 
 namespace rbgs {
@@ -28,7 +35,7 @@ __global__ void __launch_bounds__(kSweepThreads)
 residual_colour_kernel(const double *__restrict__ self, const double *__restrict__ other,
                        const double *__restrict__ hf, int n, int W, int kact,
                        int rows_per_block, double *__restrict__ partials, float *__restrict__ r32,
-                       int W32, double scale) {
+                       int W32, double scale, double one) {
     __shared__ double red_smem[kSweepThreads / 32];
     const int lane = threadIdx.x & 31;
     const int k0 = 2 * (blockIdx.x * kSweepThreads + threadIdx.x);
@@ -58,15 +65,15 @@ residual_colour_kernel(const double *__restrict__ self, const double *__restrict
             }
             const int j0 = 2 * k0 + p;
             if (act && j0 >= 1 && j0 <= n) {
-                double s = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(f2.x, up.x), dn.x), w0), e0);
-                double r = __dadd_rn(s, -__dmul_rn(4.0, me.x));
+                const double s = add_fma(add_fma(add_fma(add_fma(f2.x, up.x, one), dn.x, one), w0, one), e0, one);
+                const double r = __fma_rn(-4.0, me.x, s);
                 acc = __fma_rn(r, r, acc);
                 if (MAX) mx = fmax(mx, fabs(r));
                 if (WRITE) r32[(size_t)i * W32 + k0] = __double2float_rn(__dmul_rn(r, scale));
             }
             if (act && j0 + 2 <= n) {
-                double s = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(f2.y, up.y), dn.y), w1), e1);
-                double r = __dadd_rn(s, -__dmul_rn(4.0, me.y));
+                const double s = add_fma(add_fma(add_fma(add_fma(f2.y, up.y, one), dn.y, one), w1, one), e1, one);
+                const double r = __fma_rn(-4.0, me.y, s);
                 acc = __fma_rn(r, r, acc);
                 if (MAX) mx = fmax(mx, fabs(r));
                 if (WRITE) r32[(size_t)i * W32 + k0 + 1] = __double2float_rn(__dmul_rn(r, scale));
@@ -112,22 +119,31 @@ __device__ __forceinline__ double at(const double *const *u, int W, int i, int j
 struct ColourPtrs { const double *p[2]; };
 
 // Partial sums of (h^2 b)^2: h2f plus, in N, S, W, E order, the neighbours on the ring.
+// Thread k of block (x, y) walks element k of both colour rows down the block's rows.
 __global__ void __launch_bounds__(256)
-rhs_norm_kernel(ColourPtrs u, ColourPtrs hf, int n, int W, double *__restrict__ partials) {
+rhs_norm_kernel(ColourPtrs u, ColourPtrs hf, int n, int W, int kact, int rows_per_block,
+                double *__restrict__ partials) {
     __shared__ double smem[256 / 32];
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const int i0 = 1 + blockIdx.y * rows_per_block, i1 = min(n, i0 + rows_per_block - 1);
     double acc = 0.0;
-    const size_t total = (size_t)n * n;
-    for (size_t q = (size_t)blockIdx.x * 256 + threadIdx.x; q < total; q += (size_t)gridDim.x * 256) {
-        const int i = 1 + (int)(q / n), j = 1 + (int)(q % n);
-        double b = at(hf.p, W, i, j);
-        if (i == 1) b = __dadd_rn(b, at(u.p, W, 0, j));
-        if (i == n) b = __dadd_rn(b, at(u.p, W, n + 1, j));
-        if (j == 1) b = __dadd_rn(b, at(u.p, W, i, 0));
-        if (j == n) b = __dadd_rn(b, at(u.p, W, i, n + 1));
-        acc = __fma_rn(b, b, acc);
+    if (k < kact) {
+        for (int i = i0; i <= i1; ++i) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int j = 2 * k + ((i + c) & 1);  // natural column of element k, colour c
+                if (j < 1 || j > n) continue;
+                double b = hf.p[c][(size_t)i * W + k];
+                if (i == 1) b = __dadd_rn(b, at(u.p, W, 0, j));
+                if (i == n) b = __dadd_rn(b, at(u.p, W, n + 1, j));
+                if (j == 1) b = __dadd_rn(b, at(u.p, W, i, 0));
+                if (j == n) b = __dadd_rn(b, at(u.p, W, i, n + 1));
+                acc = __fma_rn(b, b, acc);
+            }
+        }
     }
     const double t = block_sum<256>(acc, smem);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 int residual_rows(int n, int kact) {
@@ -150,10 +166,10 @@ rbgs_status residual_passes(const rbgs_ctx *c, double scale, cudaStream_t s) {
     dim3 grid((kact + 2 * kSweepThreads - 1) / (2 * kSweepThreads), (g.n + rows - 1) / rows);
     float *r0 = WRITE ? c->f32.hf[0] : nullptr, *r1 = WRITE ? c->f32.hf[1] : nullptr;
     residual_colour_kernel<0, MAX, WRITE><<<grid, kSweepThreads, 0, s>>>(
-        c->f64.u[0], c->f64.u[1], c->f64.hf[0], g.n, g.W, kact, rows, c->partials, r0, c->f32.W, scale);
+        c->f64.u[0], c->f64.u[1], c->f64.hf[0], g.n, g.W, kact, rows, c->partials, r0, c->f32.W, scale, 1.0);
     RBGS_LAUNCH_CHECK();
     residual_colour_kernel<1, MAX, WRITE><<<grid, kSweepThreads, 0, s>>>(
-        c->f64.u[1], c->f64.u[0], c->f64.hf[1], g.n, g.W, kact, rows, c->partials, r1, c->f32.W, scale);
+        c->f64.u[1], c->f64.u[0], c->f64.hf[1], g.n, g.W, kact, rows, c->partials, r1, c->f32.W, scale, 1.0);
     RBGS_LAUNCH_CHECK();
     const int count = 2 * (int)(grid.x * grid.y);
     final_sum_kernel<<<1, kFinalThreads, 0, s>>>(c->partials, count, c->dsum);
@@ -180,12 +196,14 @@ rbgs_status launch_defect(const rbgs_ctx *c, bool write_r32, double scale, cudaS
 rbgs_status launch_rhs_norm(const rbgs_ctx *c, cudaStream_t s) {
     const Geometry &g = c->g;
     ColourPtrs u{{c->f64.u[0], c->f64.u[1]}}, hf{{c->f64.hf[0], c->f64.hf[1]}};
-    size_t total = (size_t)g.n * g.n;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 1024) blocks = 1024;
-    rhs_norm_kernel<<<blocks, 256, 0, s>>>(u, hf, g.n, g.W, c->partials);
+    const int kact = active_width(g.n);
+    const int bx = (kact + 255) / 256;
+    int rows = 16;
+    while ((size_t)bx * ((g.n + rows - 1) / rows) > (size_t)kMaxPartials) rows *= 2;
+    const dim3 grid(bx, (g.n + rows - 1) / rows);
+    rhs_norm_kernel<<<grid, 256, 0, s>>>(u, hf, g.n, g.W, kact, rows, c->partials);
     RBGS_LAUNCH_CHECK();
-    final_sum_kernel<<<1, kFinalThreads, 0, s>>>(c->partials, blocks, c->dsum + 1);
+    final_sum_kernel<<<1, kFinalThreads, 0, s>>>(c->partials, (int)(grid.x * grid.y), c->dsum + 1);
     RBGS_LAUNCH_CHECK();
     return RBGS_OK;
 }
