@@ -16,6 +16,8 @@
 // each step correctly rounded in binary32, so the result is bit-identical to them.  All
 // blocks of the cluster run the same number of barriers (the sweep count is a kernel
 // argument); nothing waits on anything outside the cluster.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace rbgs {
@@ -121,10 +123,11 @@ template <int CS>
 bool cluster_fits(int n, int W) {
     // largest shared memory per block known to fit, per CS (the occupancy query runs once
     // per new maximum)
-    static int checked_bytes = -1;
+    static std::atomic<int> checked_bytes{-1};
     const size_t smem = cluster_smem<CS>(n, W);
     if (smem > 200 * 1024) return false;
-    if (checked_bytes >= 0 && smem <= (size_t)checked_bytes) return true;
+    const int known = checked_bytes.load();
+    if (known >= 0 && smem <= (size_t)known) return true;
     if (cudaFuncSetAttribute(cluster_sweeps_f32<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
             cudaSuccess ||
         (CS > 8 && cudaFuncSetAttribute(cluster_sweeps_f32<CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
@@ -148,7 +151,9 @@ bool cluster_fits(int n, int W) {
         cudaGetLastError();
         return false;
     }
-    if ((int)smem > checked_bytes) checked_bytes = (int)smem;
+    int prev = checked_bytes.load();
+    while ((int)smem > prev && !checked_bytes.compare_exchange_weak(prev, (int)smem)) {
+    }
     return true;
 }
 

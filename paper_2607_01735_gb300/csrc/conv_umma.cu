@@ -546,13 +546,15 @@ __global__ void __launch_bounds__(kThreads, 1) conv_umma_kernel(const UArgs a) {
 
 // ------------------------------------------------------------------ host side
 int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+    static const int sms = [] {  // initialised once, thread-safely
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            v = 1;
+        }
+        return v > 0 ? v : 1;
+    }();
     return sms;
 }
 
@@ -585,12 +587,10 @@ void finish_args(UArgs &a, int B) {
 
 template <int MODE>
 rbgs_status launch(const UArgs &a, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        RBGS_CUDA(cudaFuncSetAttribute(conv_umma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kMaxSmem));
-        attr_set = true;
-    }
+    // set once per kernel instance, thread-safely; a failure is reported on every call
+    static const cudaError_t attr = cudaFuncSetAttribute(conv_umma_kernel<MODE>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    RBGS_CUDA(attr);
     const size_t smem = (size_t)a.stages * (UM + a.bn) * UK * 2 + 1024;
     const int grid = a.num_tiles < sm_count() ? a.num_tiles : sm_count();
     conv_umma_kernel<MODE><<<grid, kThreads, smem, s>>>(a);

@@ -242,12 +242,10 @@ rbgs_status run_pass(ColourField<T> &fld, int *status, cudaStream_t s) {
         fld.maps_box_w = C::EK;
         fld.maps_box_h = C::ER;
     }
-    static bool attr_set = false;  // per template instance
-    if (!attr_set) {
-        RBGS_CUDA(cudaFuncSetAttribute(temporal_tile<T, K, TR, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)C::SMEM));
-        attr_set = true;
-    }
+    // set once per template instance, thread-safely; a failure is reported on every call
+    static const cudaError_t attr = cudaFuncSetAttribute(temporal_tile<T, K, TR, TK>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    RBGS_CUDA(attr);
     const int kact = ((n + 3) / 2 + C::ALIGN - 1) / C::ALIGN * C::ALIGN;
     dim3 grid((kact + TK - 1) / TK, (n + 2 + TR - 1) / TR);
     temporal_tile<T, K, TR, TK><<<grid, kTThreads, C::SMEM, s>>>(fld.maps[0], fld.maps[1], fld.maps[4],

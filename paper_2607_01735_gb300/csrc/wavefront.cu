@@ -280,15 +280,15 @@ __global__ void __launch_bounds__(kWfThreads) wavefront_kernel(const WfArgs<T> a
 }
 
 int sm_count_wf() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+    static const int sms = [] {  // initialised once, thread-safely
+        int dev = 0, v = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
             cudaGetLastError();
-            sms = 152;
+            v = 152;
         }
-    }
+        return v;
+    }();
     return sms;
 }
 
@@ -307,15 +307,16 @@ rbgs_status run_wavefront(ColourField<T> &fld, cudaStream_t s) {
     // segments: as many as fill the warps that can be resident at once (one wave: a
     // second, partial wave would leave most SMs idle), each at least 8K rows tall so that
     // the 4K extra rows a segment marches stay a small share
-    static int per_sm = 0;  // resident blocks per SM, per template instance
-    if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wavefront_kernel<T, K>, kWfThreads, 0) !=
+    static const int per_sm = [] {  // resident blocks per SM, per template instance
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, wavefront_kernel<T, K>, kWfThreads, 0) !=
                 cudaSuccess ||
-            per_sm < 1) {
+            v < 1) {
             cudaGetLastError();
-            per_sm = 1;
+            v = 1;
         }
-    }
+        return v;
+    }();
     const long capacity = (long)per_sm * kWfWarps * sm_count_wf();
     long want = capacity / a.strips;
     if (want < 1) want = 1;
