@@ -373,16 +373,16 @@ bool tma_conv_launch(const uint16_t *src, const uint16_t *wts, const float *bias
             return true;
         }
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(conv_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kTmaRing + 1024)) != cudaSuccess) {
-            cudaGetLastError();
-            set_error("cudaFuncSetAttribute failed for the TMA convolution");
-            *st = RBGS_ECUDA;
-            return true;
-        }
-        attr_set = true;
+    static const cudaError_t attr = [] {  // set once per instance, thread-safely
+        const cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(kTmaRing + 1024));
+        if (e != cudaSuccess) cudaGetLastError();
+        return e;
+    }();
+    if (attr != cudaSuccess) {
+        set_error("cudaFuncSetAttribute failed for the TMA convolution");
+        *st = RBGS_ECUDA;
+        return true;
     }
     const size_t smem = (size_t)a.stages * stage_bytes + 1024;
     const int grid = a.num_tiles < sm_count() ? a.num_tiles : sm_count();

@@ -137,21 +137,21 @@ __global__ void __launch_bounds__(kPThreads) persistent_sweeps(const PArgs<T> a)
 // Blocks the grid needs (at most what can be resident at once).
 template <typename T, int NP>
 int persistent_grid(int n) {
-    static int per_sm = 0, sms = 0;
-    if (!per_sm) {
-        int dev = 0;
+    // resident blocks of the whole GPU, per template instance (initialised once, thread-safely;
+    // 0 when the query fails)
+    static const long cap = [] {
+        int dev = 0, sms = 0, per_sm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_sweeps<T, NP>, kPThreads, 0) !=
                 cudaSuccess) {
             cudaGetLastError();
-            per_sm = 0;
-            return 0;
+            return 0L;
         }
-    }
+        return (long)per_sm * sms;
+    }();
     const long items = (long)n * ((active_width(n) + 2 * NP - 1) / (2 * NP));
     const long want = (items + kPThreads - 1) / kPThreads;
-    const long cap = (long)per_sm * sms;
     return (int)(want < cap ? want : cap);
 }
 
