@@ -49,7 +49,10 @@ typedef enum {
     RBGS_ENONFINITE = 5,  /* the residual became NaN or Inf                              */
     RBGS_ETIMEOUT = 6     /* a bounded device-side wait gave up: the grid barrier of the
                              cooperative FP64 launch or the TMA wait of the temporal
-                             kernel (reported at the next synchronising call)             */
+                             kernel (reported by the next rbgs_residual or rbgs_solve).
+                             Sticky: the iterate is left part-updated and every later
+                             rbgs_residual / rbgs_solve on the context returns it again;
+                             destroy the context                                          */
 } rbgs_status;
 
 typedef enum {
