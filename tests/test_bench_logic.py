@@ -1,5 +1,6 @@
-"""Host logic of bench.py that mirrors the library: the sizes at which the library picks
-the cooperative FP64 launch, and the kernel each option resolves to.  No GPU needed."""
+"""Host logic of bench.py: the sizes at which the library picks the cooperative FP64 launch,
+the kernel each option resolves to, the committed ncu summaries it reads traffic from, and
+the clock-sample summary.  No GPU needed."""
 import argparse
 import importlib.util
 import os
@@ -46,3 +47,37 @@ def test_kernel_resolution():
     assert b.resolved_kernel(16384, True, 0, 0) == (3, 4)       # FP32 wavefront above 2048
     assert b.resolved_kernel(1000, True, 0, 0) == (1, 1)
     assert b.resolved_kernel(16384, False, 4, 0) == (1, 1)
+
+
+def test_committed_profiles_match_the_kernel_sources():
+    """bench.py reports a kernel's DRAM traffic only from an ncu summary taken of the current
+    sources; each committed summary must match them and hold a plausible figure (at least the
+    24 B per update that one half-sweep of 16384^2 must move, and not far above it)."""
+    b = _bench()
+    algorithmic = 24.0 * 16384 * 16384 / 2
+    for kname in b.PROFILES:
+        traffic = b.profiled_traffic(kname, -1)
+        assert traffic is not None, kname
+        assert 1.0 <= traffic / algorithmic < 1.1, (kname, traffic)
+        assert b.profiled_traffic(kname, 0x11) is None  # another arithmetic form: not reported
+
+
+def test_clock_summary_reads_throttle_reasons(tmp_path):
+    b = _bench()
+    rows = [
+        "0, GPU-aaa, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, GPU-aaa, 2040, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, GPU-aaa, 2055, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "1, GPU-bbb, 1200, 2070, 300.0, 0x40, Not Active, Active, Not Active, Not Active",  # other GPU
+        "garbled line",
+    ]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    s = b.ClockSampler("GPU-aaa")
+    s.path = str(path)
+    s.proc = object()  # as if nvidia-smi had run
+    got = s.summary()
+    assert got["sm_mhz"] == 2055 and got["sm_max_mhz"] == 2070 and got["samples"] == 3
+    assert got["reasons"] == ["sw_power_cap"]
+    s.uuid = None  # every GPU's rows
+    assert s.summary()["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
