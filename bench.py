@@ -839,18 +839,21 @@ def main():
     kernel, kdepth = resolved_kernel(n, refine, args.kernel, args.tblock_k)
     blocked = kernel in (2, 3)  # several sweeps per launch (TMA tiles or register wavefront)
     persistent = uses_persistent(args, n, refine)
-    # pack f, pack u, ||b|| (2), the sweeps, residual (3), unpack
+    # pack f, pack u, ||b|| (2), the sweeps, residual, unpack.  The residual after FP64
+    # sweeps walks the red points only (2 launches: the black rt is exactly zero), else both
+    # colours (3)
+    resid = 2 if sweeps > 0 else 3
     if refine:
         inner = args.inner or 100
         outer = -(-sweeps // inner)
         per_outer = 4 + 1 + 3 + (inner // kdepth + 2 * (inner % kdepth) if blocked else 2 * inner)
         launches_per_step = 4 + 4 + outer * per_outer + 3 + 1
     elif blocked:
-        launches_per_step = 4 + sweeps // kdepth + 2 * (sweeps % kdepth) + 3 + 1
+        launches_per_step = 4 + sweeps // kdepth + 2 * (sweeps % kdepth) + resid + 1
     elif persistent:  # one cooperative launch runs all the sweeps (up to 2^20 per launch)
-        launches_per_step = 4 + -(-sweeps // (1 << 20)) + 3 + 1
+        launches_per_step = 4 + -(-sweeps // (1 << 20)) + resid + 1
     else:
-        launches_per_step = 4 + 2 * sweeps + 3 + 1
+        launches_per_step = 4 + 2 * sweeps + resid + 1
 
     for _ in range(args.warmup):
         step(f, u0, out)

@@ -76,6 +76,7 @@ rbgs_status stage_in(rbgs_ctx *c, const double *src, size_t count, const double 
 
 rbgs_status load_problem(rbgs_ctx *c, const double *f, const double *u_init) {
     const Geometry &g = c->g;
+    c->black_fresh = false;
     const double *view = nullptr;
     rbgs_status st;
     if (f) {
@@ -205,6 +206,21 @@ rbgs_status ensure_graph(rbgs_ctx *c) {
     return RBGS_OK;
 }
 
+// nsweeps FP64 sweeps: one cooperative launch, cached graphs of kGraphSweeps sweeps on small
+// grids, or direct / temporally blocked launches.
+rbgs_status sweeps_f64(rbgs_ctx *c, long nsweeps) {
+    if (use_persistent(c)) return launch_persistent_sweeps<double>(c->f64, nsweeps, c->pcounter, c->dstatus, c->stream);
+    if (c->kernel == RBGS_KERNEL_COLOUR && c->g.n <= kGraphMaxN && nsweeps >= kGraphSweeps) {
+        rbgs_status st = ensure_graph(c);
+        if (st != RBGS_OK) return st;
+        while (nsweeps >= c->graph_sweeps) {
+            RBGS_CUDA(cudaGraphLaunch(c->graph, c->stream));
+            nsweeps -= c->graph_sweeps;
+        }
+    }
+    return enqueue_sweeps(c, nsweeps, c->stream);
+}
+
 // rho and max |rt| of the current FP64 iterate (synchronises the stream).
 rbgs_status defect_stats(rbgs_ctx *c, double *rho, double *mx) {
     rbgs_status st = launch_defect(c, false, 1.0, c->stream);
@@ -268,6 +284,7 @@ rbgs_status inner_sweeps_f32(rbgs_ctx *c, long m) {
 
 // Mixed-precision iterative refinement: FP64 defect and correction, FP32 sweeps.
 rbgs_status refine_solve(rbgs_ctx *c, double tol, long *done_out, double *rho_out) {
+    c->black_fresh = false;  // the corrections move every point
     rbgs_status st = ensure_f32(c);
     long done = 0;
     double rho = 0.0, mx = 0.0;
@@ -471,16 +488,11 @@ rbgs_status rbgs_sweep(rbgs_t c, long nsweeps) {
     clear_error();
     if (!c) { set_error("ctx is NULL"); return RBGS_EINVAL; }
     if (nsweeps < 0) { set_error("nsweeps < 0"); return RBGS_EINVAL; }
-    if (use_persistent(c)) return launch_persistent_sweeps<double>(c->f64, nsweeps, c->pcounter, c->dstatus, c->stream);
-    if (c->kernel == RBGS_KERNEL_COLOUR && c->g.n <= kGraphMaxN && nsweeps >= kGraphSweeps) {
-        rbgs_status st = ensure_graph(c);
-        if (st != RBGS_OK) return st;
-        while (nsweeps >= c->graph_sweeps) {
-            RBGS_CUDA(cudaGraphLaunch(c->graph, c->stream));
-            nsweeps -= c->graph_sweeps;
-        }
-    }
-    return enqueue_sweeps(c, nsweeps, c->stream);
+    if (nsweeps == 0) return RBGS_OK;
+    const rbgs_status st = sweeps_f64(c, nsweeps);
+    // after a completed sweep the black points' residual is exactly zero (residual.cu)
+    c->black_fresh = st == RBGS_OK;
+    return st;
 }
 
 rbgs_status rbgs_residual(rbgs_t c, double *rel) {

@@ -297,13 +297,17 @@ __device__ void block_half_sweep_f32(const DevProblem &P, int vt) {
     block_half_sweep_band<float, C, VT, CS>(P.d[C], P.d[C ^ 1], P.r[C], P.n, P.W32, vt);
 }
 
-// Per-thread partial of sum rt^2 (and max |rt|; optionally write (float)(rt * scale)).
+// Per-thread partial of sum rt^2 (and max |rt|; optionally write (float)(rt * scale)) over
+// the first `colours` colours.  Right after a full FP64 sweep the black points' rt is exactly
+// zero (their values are s * 0.25 of the very sums s formed here, and 4 (s * 0.25) = s), so
+// the red points alone give the same sum bit for bit: colours = 1 there.
 template <int VT, int CS, bool WRITE>
-__device__ void block_residual(const DevProblem &P, double scale, double &r2, double &mx, int vt) {
+__device__ void block_residual(const DevProblem &P, double scale, double &r2, double &mx, int vt,
+                               int colours = 2) {
     const int n = P.n, W = P.W, kact = kact_of(n);
     r2 = 0.0;
     mx = 0.0;
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < colours; ++c) {
         const double *self = P.u[c], *other = P.u[c ^ 1], *hf = P.hf[c];
         const int items = n * kact;
         for (int q = vt; q < items; q += VT) {
@@ -414,7 +418,8 @@ __device__ void solve_problem(const DevProblem &P, DevResult &R, double tol, int
             team_sync<CS>();
             done += k;
         }
-        block_residual<VT, CS, false>(P, 1.0, r2, mx, vt);
+        // after FP64 sweeps the black rt is zero; the refinement's correction moves every point
+        block_residual<VT, CS, false>(P, 1.0, r2, mx, vt, refine ? 2 : 1);
         r2 = team_sum<THREADS, CS>(r2, smem, slot);
         mx = team_max<THREADS, CS>(mx, smem, slot);
         rho = rho_of(r2, den2);

@@ -104,7 +104,8 @@ struct rbgs_ctx {
     int inner_sweeps;           // resolved FP32 sweeps per correction
     int kernel32;               // resolved inner kernel for the FP32 sweeps
     int *hstatus;               // pinned host mirror of dstatus
-    unsigned *pcounter;         // device: grid-barrier counter of the persistent small-grid sweeps
+    unsigned *pcounter;         // device: grid-barrier counter of the cooperative sweep launch
+    bool black_fresh;           // the FP64 iterate is the result of a full sweep (black rt == 0)
 };
 
 namespace rbgs {

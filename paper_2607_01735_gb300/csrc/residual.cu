@@ -16,6 +16,13 @@
 // rhs_norm_kernel (h2f plus the ring neighbours of each boundary-adjacent point), walking
 // the colour rows without any index division.
 //
+// Right after a full sweep the black points' rt is exactly zero: each black value was set
+// to s * 0.25 from the very sum s the residual forms (the red values have not moved since),
+// and 4 (s * 0.25) = s exactly (where s * 0.25 is subnormal and rounded, |rt| < 2^-1072 and
+// its square adds nothing to the sum).  The red-black ordering gives this for any right-hand
+// side (Section 2, Eq. (1)).  So after a sweep only the red points are walked: half the
+// work, and the same sum bit for bit (the black partials were exact zeros).
+//
 // The same walk also serves the mixed-precision refinement: max |rt| (exact, order-
 // independent) and the FP32 scaled defect (float)(rt * 2^-e) for the inner solver.
 #include "common.cuh"
@@ -158,8 +165,10 @@ int residual_rows(int n, int kact) {
 
 namespace {
 
+// red_only: the black points' rt is known to be zero (the iterate is the result of a full
+// sweep); only the red partials are formed and summed.
 template <bool MAX, bool WRITE>
-rbgs_status residual_passes(const rbgs_ctx *c, double scale, cudaStream_t s) {
+rbgs_status residual_passes(const rbgs_ctx *c, double scale, cudaStream_t s, bool red_only) {
     const Geometry &g = c->g;
     const int kact = active_width(g.n);
     const int rows = residual_rows(g.n, kact);
@@ -168,10 +177,12 @@ rbgs_status residual_passes(const rbgs_ctx *c, double scale, cudaStream_t s) {
     residual_colour_kernel<0, MAX, WRITE><<<grid, kSweepThreads, 0, s>>>(
         c->f64.u[0], c->f64.u[1], c->f64.hf[0], g.n, g.W, kact, rows, c->partials, r0, c->f32.W, scale, 1.0);
     RBGS_LAUNCH_CHECK();
-    residual_colour_kernel<1, MAX, WRITE><<<grid, kSweepThreads, 0, s>>>(
-        c->f64.u[1], c->f64.u[0], c->f64.hf[1], g.n, g.W, kact, rows, c->partials, r1, c->f32.W, scale, 1.0);
-    RBGS_LAUNCH_CHECK();
-    const int count = 2 * (int)(grid.x * grid.y);
+    if (!red_only) {
+        residual_colour_kernel<1, MAX, WRITE><<<grid, kSweepThreads, 0, s>>>(
+            c->f64.u[1], c->f64.u[0], c->f64.hf[1], g.n, g.W, kact, rows, c->partials, r1, c->f32.W, scale, 1.0);
+        RBGS_LAUNCH_CHECK();
+    }
+    const int count = (red_only ? 1 : 2) * (int)(grid.x * grid.y);
     final_sum_kernel<<<1, kFinalThreads, 0, s>>>(c->partials, count, c->dsum);
     RBGS_LAUNCH_CHECK();
     if (MAX) {
@@ -184,13 +195,13 @@ rbgs_status residual_passes(const rbgs_ctx *c, double scale, cudaStream_t s) {
 }  // namespace
 
 rbgs_status launch_residual_sum(const rbgs_ctx *c, cudaStream_t s) {
-    return residual_passes<false, false>(c, 1.0, s);
+    return residual_passes<false, false>(c, 1.0, s, c->black_fresh);
 }
 
 // write_r32 = false: sum rt^2 -> dsum[0], max |rt| -> dsum[2].
 // write_r32 = true:  r32 = (float)(rt * scale) at interior points (and the sum again).
 rbgs_status launch_defect(const rbgs_ctx *c, bool write_r32, double scale, cudaStream_t s) {
-    return write_r32 ? residual_passes<false, true>(c, scale, s) : residual_passes<true, false>(c, scale, s);
+    return write_r32 ? residual_passes<false, true>(c, scale, s, false) : residual_passes<true, false>(c, scale, s, false);
 }
 
 rbgs_status launch_rhs_norm(const rbgs_ctx *c, cudaStream_t s) {

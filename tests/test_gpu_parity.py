@@ -205,6 +205,68 @@ def test_residual_zero_rhs_is_absolute():
     assert abs(rho - oracle.residual(u, f, synth.h_squared(n))[0]) <= 1e-12 * rho
 
 
+@pytest.mark.parametrize("kernel", [rb.RBGS_KERNEL_COLOUR, rb.RBGS_KERNEL_PERSISTENT, rb.RBGS_KERNEL_TEMPORAL,
+                                    rb.RBGS_KERNEL_WAVEFRONT])
+@pytest.mark.parametrize("n", [1, 2, 5, 64, 257])
+def test_residual_after_sweeps_walks_red_only_with_the_same_bits(kernel, n):
+    """After a full sweep the library sums rt^2 over the red points only: the black rt is
+    exactly zero there (the black values are s/4 of the very sums the residual forms).  The
+    same iterate reloaded (so nothing is known of it) takes the walk over both colours; the
+    two norms must agree bit for bit, and with the oracle's."""
+    h2 = synth.h_squared(n)
+    f, u0 = _problem(n, 85)
+    fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u0).cuda()
+    out = torch.empty_like(ud)
+    with rb.Solver(n, h2, fd, ud, kernel=kernel) as s:
+        s.sweep(4)
+        rho_red = s.residual()
+        s.get_solution(out)
+        s.set_solution(out)
+        rho_full = s.residual()
+        s.sweep(0)  # no sweep: the state stays unknown
+        assert s.residual() == rho_full
+    assert np.float64(rho_red).view(np.uint64) == np.float64(rho_full).view(np.uint64)
+    ref = u0.copy()
+    oracle.sweeps(ref, f, h2, 4)
+    _assert_bits(out.cpu().numpy(), ref)
+    rho_ref = oracle.residual(ref, f, h2)[0]
+    assert abs(rho_red - rho_ref) <= RESID_RTOL * rho_ref
+
+
+def test_red_only_residual_with_subnormal_black_values():
+    """A region of the grid where h^2 f and the iterate are subnormal: there the black
+    values s * 0.25 are rounded, so the black rt is not exactly zero, but below 2^-1072, and
+    its square adds nothing to the sum.  The red-only and two-colour norms agree bit for bit."""
+    n = 64
+    h2 = synth.h_squared(n)
+    f = synth.uniform_pm1_grid(n, 86).numpy().copy()
+    f[:, n // 2:] *= 1e-310   # right half: h^2 f and, after 3 sweeps, u on its far side subnormal
+    u0 = np.zeros((n + 2, n + 2))
+    fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u0).cuda()
+    out = torch.empty_like(ud)
+    with rb.Solver(n, h2, fd, ud, kernel=rb.RBGS_KERNEL_COLOUR) as s:
+        s.sweep(3)
+        rho_red = s.residual()
+        s.get_solution(out)
+        s.set_solution(out)
+        rho_full = s.residual()
+    got = out.cpu().numpy()
+    tiny = got[1:-1, 1:-1][:, -16:]
+    assert np.all(np.abs(tiny) < np.finfo(np.float64).tiny) and np.any(tiny != 0)
+    # the premise: some black rt is not zero (s * 0.25 rounded), each far below 2^-1072
+    s_ = h2 * f + got[:-2, 1:-1] + got[2:, 1:-1] + got[1:-1, :-2] + got[1:-1, 2:]
+    rt = s_ - 4.0 * got[1:-1, 1:-1]
+    i, j = np.indices((n, n)) + 1
+    black = rt[(i + j) % 2 == 1]
+    assert np.any(black != 0) and np.all(np.abs(black) < 2.0 ** -1072)
+    assert np.float64(rho_red).view(np.uint64) == np.float64(rho_full).view(np.uint64)
+    ref = u0.copy()
+    oracle.sweeps(ref, f, h2, 3)
+    _assert_bits(got, ref)
+    rho_ref = oracle.residual(ref, f, h2)[0]
+    assert abs(rho_red - rho_ref) <= RESID_RTOL * rho_ref
+
+
 def test_solve_matches_oracle_sweep_count():
     n = 63
     f, u0 = _problem(n, 77, interior=False)
