@@ -126,30 +126,59 @@ __device__ __forceinline__ double at(const double *const *u, int W, int i, int j
 struct ColourPtrs { const double *p[2]; };
 
 // Partial sums of (h^2 b)^2: h2f plus, in N, S, W, E order, the neighbours on the ring.
-// Thread k of block (x, y) walks element k of both colour rows down the block's rows.
-__global__ void __launch_bounds__(256)
+// Thread t of block (x, y) takes elements k0 = 2t and k0 + 1 of both colour rows (one 16-byte
+// load per colour row) down the block's rows, loading four rows ahead of their use so that
+// eight loads are in flight.  Away from the first and last interior row and column, b is h2f
+// itself (no ring neighbour), so those rows take four fused multiply-adds and no index
+// arithmetic: the walk is bound by HBM, not by instruction issue.
+constexpr int kNormThreads = 256;
+constexpr int kNormRowsAhead = 4;
+
+__global__ void __launch_bounds__(kNormThreads)
 rhs_norm_kernel(ColourPtrs u, ColourPtrs hf, int n, int W, int kact, int rows_per_block,
                 double *__restrict__ partials) {
-    __shared__ double smem[256 / 32];
-    const int k = blockIdx.x * 256 + threadIdx.x;
+    __shared__ double smem[kNormThreads / 32];
+    const int k0 = 2 * (blockIdx.x * kNormThreads + threadIdx.x);
     const int i0 = 1 + blockIdx.y * rows_per_block, i1 = min(n, i0 + rows_per_block - 1);
+    // this thread's columns 2 k0 + {0..3} all lie in 2..n-1
+    const bool inner_cols = k0 > 0 && 2 * k0 + 3 < n;
     double acc = 0.0;
-    if (k < kact) {
-        for (int i = i0; i <= i1; ++i) {
+    if (k0 < kact) {  // k0 + 1 < W always (W is even and at least kact)
+        for (int i = i0; i <= i1; i += kNormRowsAhead) {
+            double2 v[kNormRowsAhead][2];
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int j = 2 * k + ((i + c) & 1);  // natural column of element k, colour c
-                if (j < 1 || j > n) continue;
-                double b = hf.p[c][(size_t)i * W + k];
-                if (i == 1) b = __dadd_rn(b, at(u.p, W, 0, j));
-                if (i == n) b = __dadd_rn(b, at(u.p, W, n + 1, j));
-                if (j == 1) b = __dadd_rn(b, at(u.p, W, i, 0));
-                if (j == n) b = __dadd_rn(b, at(u.p, W, i, n + 1));
-                acc = __fma_rn(b, b, acc);
+            for (int r = 0; r < kNormRowsAhead; ++r) {
+                const size_t row = (size_t)min(i + r, i1) * W;  // rows past i1: reloaded, unused
+                v[r][0] = ldg2(hf.p[0] + row + k0);
+                v[r][1] = ldg2(hf.p[1] + row + k0);
+            }
+#pragma unroll
+            for (int r = 0; r < kNormRowsAhead; ++r) {
+                const int ii = i + r;
+                if (ii > i1) break;
+                if (inner_cols && ii > 1 && ii < n) {
+                    acc = __fma_rn(v[r][0].x, v[r][0].x, acc);
+                    acc = __fma_rn(v[r][0].y, v[r][0].y, acc);
+                    acc = __fma_rn(v[r][1].x, v[r][1].x, acc);
+                    acc = __fma_rn(v[r][1].y, v[r][1].y, acc);
+                    continue;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = q >> 1, k = k0 + (q & 1);
+                    const int j = 2 * k + ((ii + c) & 1);  // natural column of element k, colour c
+                    if (j < 1 || j > n) continue;
+                    double b = (q & 1) ? v[r][c].y : v[r][c].x;
+                    if (ii == 1) b = __dadd_rn(b, at(u.p, W, 0, j));
+                    if (ii == n) b = __dadd_rn(b, at(u.p, W, n + 1, j));
+                    if (j == 1) b = __dadd_rn(b, at(u.p, W, ii, 0));
+                    if (j == n) b = __dadd_rn(b, at(u.p, W, ii, n + 1));
+                    acc = __fma_rn(b, b, acc);
+                }
             }
         }
     }
-    const double t = block_sum<256>(acc, smem);
+    const double t = block_sum<kNormThreads>(acc, smem);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
@@ -208,11 +237,11 @@ rbgs_status launch_rhs_norm(const rbgs_ctx *c, cudaStream_t s) {
     const Geometry &g = c->g;
     ColourPtrs u{{c->f64.u[0], c->f64.u[1]}}, hf{{c->f64.hf[0], c->f64.hf[1]}};
     const int kact = active_width(g.n);
-    const int bx = (kact + 255) / 256;
+    const int bx = (kact + 2 * kNormThreads - 1) / (2 * kNormThreads);
     int rows = 16;
     while ((size_t)bx * ((g.n + rows - 1) / rows) > (size_t)kMaxPartials) rows *= 2;
     const dim3 grid(bx, (g.n + rows - 1) / rows);
-    rhs_norm_kernel<<<grid, 256, 0, s>>>(u, hf, g.n, g.W, kact, rows, c->partials);
+    rhs_norm_kernel<<<grid, kNormThreads, 0, s>>>(u, hf, g.n, g.W, kact, rows, c->partials);
     RBGS_LAUNCH_CHECK();
     final_sum_kernel<<<1, kFinalThreads, 0, s>>>(c->partials, (int)(grid.x * grid.y), c->dsum + 1);
     RBGS_LAUNCH_CHECK();
