@@ -249,6 +249,30 @@ def test_black_residual_exactly_zero_after_full_sweep():
     assert np.all(r[(i + j) % 2 == 0] != 0.0)
 
 
+def test_red_points_alone_give_the_residual_sum_bit_for_bit():
+    """After a full sweep the sum of rt^2 over the red points alone equals the oracle's sum
+    over all points, bit for bit, also where the iterate is subnormal: there s * 0.25 is
+    rounded, so a black rt need not be zero, but it stays below 2^-1072 and its square
+    rounds to zero.  (The library's residual walks only the red points after a sweep.)"""
+    n = 64
+    h2 = synth.h_squared(n)
+    f = synth.uniform_pm1_grid(n, 86).numpy().copy()
+    f[:, n // 2:] *= 1e-310
+    u = np.zeros((n + 2, n + 2))
+    oracle.sweeps(u, f, h2, 3)
+    r = oracle.residual_field(u, f, h2)
+    i, j = np.meshgrid(np.arange(1, n + 1), np.arange(1, n + 1), indexing="ij")
+    black = r[(i + j) % 2 == 1]
+    assert np.any(black != 0.0) and np.all(np.abs(black) < 2.0 ** -1072)
+    _, r2_all, _ = oracle.residual(u, f, h2)
+    acc = 0.0
+    for ii in range(n):          # the oracle's i-major order, red points only
+        for jj in range(n):
+            if (ii + jj) % 2 == 0:
+                acc = acc + float(r[ii, jj]) * float(r[ii, jj])
+    assert acc == r2_all and acc > 0.0
+
+
 def test_residual_of_zero_guess_is_one_and_of_exact_solution_tiny():
     n = 20
     f, _ = _random_problem(n, 700, ring=False)
