@@ -30,6 +30,11 @@
  * errors from a failed launch leave the context usable only for rbgs_destroy.
  * Work is ordered on the stream given at creation (NULL = the legacy default stream);
  * calls that return a host scalar synchronise that stream.
+ *
+ * Devices and threads: a context lives on the device that is current when rbgs_create
+ * runs; call it with that device current (the library does not switch devices).  Calls
+ * on one context must not overlap in time; separate contexts may be used from separate
+ * threads at once.
  */
 #ifndef RBGS_H
 #define RBGS_H
