@@ -936,34 +936,37 @@ def main():
     if not args.no_e2e:
         # End to end from pinned host memory: every step copies its f and u0 in from pinned
         # host buffers, solves, and copies the solution and rho out.  As a serving loop runs
-        # a stream of solves, the copies go on a copy stream into device buffers (double
+        # a stream of solves, the copies go on copy streams into device buffers (double
         # buffered) while the previous or next step's sweeps run; the library then loads from
         # and unpacks to device memory.  The serial figure beside it passes the host buffers
         # to the library directly, one step after another, nothing overlapped.
         fh = f.cpu().pin_memory()
         uh = u0.cpu().pin_memory()
         oh = torch.empty(n + 2, n + 2, dtype=torch.float64).pin_memory()
-        copy_stream = torch.cuda.Stream(dev)
+        # one stream per direction: host-to-device and device-to-host copies use separate
+        # copy engines and link directions, so the next inputs and the last solution move
+        # at the same time
+        in_stream, out_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         d_in = [(torch.empty_like(f), torch.empty_like(u0)) for _ in range(2)]
         d_out = [torch.empty_like(u0) for _ in range(2)]
 
         def pipelined(k):
             ev_in = [torch.cuda.Event(), torch.cuda.Event()]
             ev_out = [None, None]
-            with torch.cuda.stream(copy_stream):
+            with torch.cuda.stream(in_stream):
                 d_in[0][0].copy_(fh, non_blocking=True)
                 d_in[0][1].copy_(uh, non_blocking=True)
-                ev_in[0].record(copy_stream)
+                ev_in[0].record(in_stream)
             for i in range(k):
                 b = i % 2
                 stream.wait_event(ev_in[b])
                 rb.rbgs_set_problem(ctx_a, d_in[b][0], d_in[b][1])
                 if i + 1 < k:  # the next step's inputs, during this step's sweeps
                     nb = 1 - b
-                    with torch.cuda.stream(copy_stream):
+                    with torch.cuda.stream(in_stream):
                         d_in[nb][0].copy_(fh, non_blocking=True)
                         d_in[nb][1].copy_(uh, non_blocking=True)
-                        ev_in[nb].record(copy_stream)
+                        ev_in[nb].record(in_stream)
                 run_sweeps(ctx_a, stream)
                 rb.rbgs_residual(ctx_a)
                 if ev_out[b] is not None:
@@ -971,21 +974,23 @@ def main():
                 rb.rbgs_get_solution(ctx_a, d_out[b])
                 ready = torch.cuda.Event()
                 ready.record(stream)
-                with torch.cuda.stream(copy_stream):
-                    copy_stream.wait_event(ready)
+                with torch.cuda.stream(out_stream):
+                    out_stream.wait_event(ready)
                     oh.copy_(d_out[b], non_blocking=True)  # during the next step's sweeps
                     ev_out[b] = torch.cuda.Event()
-                    ev_out[b].record(copy_stream)
+                    ev_out[b].record(out_stream)
 
         def timed(body):
             with ClockSampler(str(uuid) if uuid else None) as clk:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                copy_stream.wait_event(e0)
+                in_stream.wait_event(e0)
+                out_stream.wait_event(e0)
                 body()
-                j = torch.cuda.Event()
-                j.record(copy_stream)
-                stream.wait_event(j)
+                for cs in (in_stream, out_stream):
+                    j = torch.cuda.Event()
+                    j.record(cs)
+                    stream.wait_event(j)
                 e1.record(stream)
                 barrier()
             et = e0.elapsed_time(e1) / 1e3
@@ -1004,8 +1009,8 @@ def main():
                "h2d_bytes_per_step": 8 * (n * n + (n + 2) * (n + 2)),
                "d2h_bytes_per_step": 8 * (n + 2) * (n + 2) + 8,
                "ms_per_step": 1e3 * et / args.steps, "clocks": e2e_clocks,
-               "pipelined": "host copies on a copy stream into double-buffered device inputs and out of "
-                            "the device solution, overlapping the neighbouring steps' sweeps",
+               "pipelined": "host copies on two copy streams (one per direction) into double-buffered device "
+                            "inputs and out of the device solution, overlapping the neighbouring steps' sweeps",
                "serial": {"value": lups / et_serial / 1e9, "ms_per_step": 1e3 * et_serial / args.steps}}
     rb.rbgs_destroy(ctx_a)
 
