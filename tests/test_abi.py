@@ -94,6 +94,34 @@ def test_argument_errors_without_gpu(lib):
     lib.rbgs_destroy(None)  # ignored
 
 
+def test_batched_argument_errors_without_gpu(lib):
+    """rbgs_solve_batched checks its arguments on the host before any CUDA call."""
+    f = np.zeros((4, 4))
+    u = np.zeros((6, 6))
+    out = np.zeros((6, 6))
+    probs = (rb.Problem * 1)(rb.Problem(4, 0.04, f.ctypes.data, u.ctypes.data))
+    outs = (ctypes.c_void_p * 1)(out.ctypes.data)
+    res = (rb.Result * 1)()
+    ok_args = (probs, 1e-8, None, None, outs, res)
+    assert lib.rbgs_solve_batched(0, None, 1e-8, None, None, None, None) == rb.RBGS_OK  # nothing to do
+    assert lib.rbgs_solve_batched(-1, *ok_args) == rb.RBGS_EINVAL
+    assert lib.rbgs_solve_batched(1, None, 1e-8, None, None, outs, res) == rb.RBGS_EINVAL
+    assert lib.rbgs_solve_batched(1, probs, 1e-8, None, None, None, res) == rb.RBGS_EINVAL
+    assert lib.rbgs_solve_batched(1, probs, 1e-8, None, None, outs, None) == rb.RBGS_EINVAL
+    assert lib.rbgs_solve_batched(1, probs, -1.0, None, None, outs, res) == rb.RBGS_EINVAL
+    assert lib.rbgs_solve_batched(1, probs, float("nan"), None, None, outs, res) == rb.RBGS_EINVAL
+    bad = rb.default_opts(precision=7)
+    assert lib.rbgs_solve_batched(1, probs, 1e-8, ctypes.byref(bad), None, outs, res) == rb.RBGS_EINVAL
+    for n, h2, fp, up in ((0, 0.04, f, u), (40000, 1e-9, f, u), (4, 0.0, f, u), (4, 0.04, None, u),
+                          (4, 0.04, f, None)):
+        bad_p = (rb.Problem * 1)(rb.Problem(n, h2, fp.ctypes.data if fp is not None else None,
+                                            up.ctypes.data if up is not None else None))
+        assert lib.rbgs_solve_batched(1, bad_p, 1e-8, None, None, outs, res) == rb.RBGS_EINVAL
+        assert "problem 0" in rb.rbgs_last_error()
+    null_out = (ctypes.c_void_p * 1)(None)
+    assert lib.rbgs_solve_batched(1, probs, 1e-8, None, None, null_out, res) == rb.RBGS_EINVAL
+
+
 def test_binding_rejects_wrong_dtypes(lib):
     with pytest.raises(TypeError):
         rb._ptr(np.zeros(4, dtype=np.float32))
