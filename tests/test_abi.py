@@ -122,6 +122,45 @@ def test_batched_argument_errors_without_gpu(lib):
     assert lib.rbgs_solve_batched(1, probs, 1e-8, None, None, null_out, res) == rb.RBGS_EINVAL
 
 
+def test_unet_and_conv_argument_errors_without_gpu(lib):
+    """The convolution and network entry points check their arguments on the host."""
+    vp, i32 = ctypes.c_void_p, ctypes.c_int
+    buf = np.zeros(4096, dtype=np.uint16)
+    base = buf.ctypes.data + (-buf.ctypes.data) % 16         # a 16-byte aligned address
+    x, w, y = vp(base), vp(base + 1024), vp(base + 2048)
+
+    def fwd(X, Wt, Y, B=1, H=8, W=8, cin=8, cout=8, ks=3):
+        return lib.rbgs_conv_forward(X, Wt, None, Y, i32(B), i32(H), i32(W), i32(cin), i32(cout),
+                                     i32(ks), i32(0), i32(0), None)
+
+    assert fwd(None, w, y) == rb.RBGS_EINVAL
+    assert fwd(x, None, y) == rb.RBGS_EINVAL
+    assert fwd(x, w, None) == rb.RBGS_EINVAL
+    assert fwd(x, w, y, cin=12) == rb.RBGS_EINVAL            # channels: multiples of 8
+    assert fwd(x, w, y, cout=4) == rb.RBGS_EINVAL
+    assert fwd(x, w, y, ks=2) == rb.RBGS_EINVAL              # 3x3 or 1x1 only
+    assert fwd(x, w, y, B=0) == rb.RBGS_EINVAL
+    assert fwd(vp(base + 2), w, y) == rb.RBGS_EINVAL         # operands 16-byte aligned
+    assert "bad arguments" in rb.rbgs_last_error()
+    dx = vp(base + 3072)
+    # a data gradient needs the transposed-weight scratch
+    assert lib.rbgs_conv_backward(x, w, y, dx, dx, None, None, i32(1), i32(8), i32(8), i32(8), i32(8),
+                                  i32(3), i32(0), None) == rb.RBGS_EINVAL
+    engine = lib.rbgs_conv_get_engine()
+    assert lib.rbgs_conv_set_engine(i32(7)) == rb.RBGS_EINVAL
+    assert lib.rbgs_conv_get_engine() == engine              # unchanged by a refused value
+    assert lib.rbgs_unet_create(ctypes.c_uint64(1), None, None) == rb.RBGS_EINVAL
+    lib.rbgs_unet_num_params.restype = ctypes.c_long
+    assert lib.rbgs_unet_num_params(None) == 0
+    p = vp(base)
+    assert lib.rbgs_unet_get_params(None, p) == rb.RBGS_EINVAL
+    assert lib.rbgs_unet_set_params(None, p) == rb.RBGS_EINVAL
+    assert lib.rbgs_unet_forward(None, p, p, i32(1), i32(8), i32(8)) == rb.RBGS_EINVAL
+    assert lib.rbgs_unet_train_step(None, p, p, p, i32(1), i32(8), i32(8), ctypes.c_float(1e-3), None,
+                                    None) == rb.RBGS_EINVAL
+    lib.rbgs_unet_destroy(None)  # ignored
+
+
 def test_binding_rejects_wrong_dtypes(lib):
     with pytest.raises(TypeError):
         rb._ptr(np.zeros(4, dtype=np.float32))
