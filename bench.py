@@ -56,7 +56,9 @@ OUT_DIR = os.environ.get("RBGS_BENCH_OUT", os.path.join(ROOT, "bench_out"))
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: 10 for the grid, as the median of 10 runs of the "
+                        "paper's measurements; 5 for the other modes)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=16384)
@@ -99,7 +101,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-ttr", action="store_true", help="skip the time-to-residual comparison")
     p.add_argument("--ttr-n", type=int, default=511, help="grid for the time-to-residual comparison")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.steps is None:
+        a.steps = 10 if a.mode == "grid" else 5
+    return a
 
 
 def workload(n, sweeps, precision="fp64"):

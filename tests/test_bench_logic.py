@@ -81,3 +81,13 @@ def test_clock_summary_reads_throttle_reasons(tmp_path):
     assert got["reasons"] == ["sw_power_cap"]
     s.uuid = None  # every GPU's rows
     assert s.summary()["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_default_step_counts(monkeypatch):
+    """The grid bench times 10 steps by default (the paper reports the median of 10 runs);
+    the other modes 5; an explicit --steps wins."""
+    b = _bench()
+    for argv, want in ((["bench.py"], 10), (["bench.py", "--impl", "reference"], 10),
+                       (["bench.py", "--mode", "batched"], 5), (["bench.py", "--steps", "3"], 3)):
+        monkeypatch.setattr("sys.argv", argv)
+        assert b.parse().steps == want
