@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--values", type=int, default=0, help="values per thread in a half-sweep (0 auto, 2, 4)")
     p.add_argument("--rows", type=int, default=0, help="rows per loop step in a half-sweep (0 auto, 1, 2)")
     p.add_argument("--int-rows", type=int, default=0, help="hybrid FP64: integer-pipe rows per strip pair")
+    p.add_argument("--fma", type=int, default=0, choices=[0, 1],
+                   help="FP64 update: 0 bit-exact, 1 fused (exact fixed-point sum, one rounding)")
     p.add_argument("--kernel", type=int, default=0,
                    help="0 auto, 1 one launch per colour, 2 temporal (TMA tiles), 3 register wavefront, "
                         "4 all sweeps in one cooperative launch (FP64)")
@@ -151,7 +153,7 @@ def profiled_traffic(kname, emulate):
 def uses_persistent(args, n, refine):
     """The FP64 sweeps run in one cooperative launch: RBGS_KERNEL_PERSISTENT, or AUTO with
     the default launch shape and PERSIST_MIN_N <= n <= PERSIST_MAX_N (the library's rule)."""
-    if refine:
+    if refine or args.fma:
         return False
     if args.kernel == 4:
         return True
@@ -799,7 +801,7 @@ def main():
                            sweep_values=args.values, sweep_rows=args.rows, int_rows=args.int_rows,
                            tblock_k=args.tblock_k,
                            precision=rb.RBGS_FP32_REFINE if refine else rb.RBGS_FP64,
-                           inner_sweeps=args.inner, max_sweeps=sweeps)
+                           inner_sweeps=args.inner, max_sweeps=sweeps, fma=args.fma)
     lib = rb.load_library()
     stream = torch.cuda.current_stream(dev)
 
@@ -847,8 +849,10 @@ def main():
     # pack f, pack u, ||b|| (2), the sweeps, residual, unpack.  The residual after FP64
     # sweeps walks the red points only (2 launches: the black rt is exactly zero), else both
     # colours (3)
-    resid = 2 if sweeps > 0 else 3
-    if refine:
+    resid = 2 if sweeps > 0 and not args.fma else 3
+    if args.fma:  # + max |h2 f| at load; per block of <= 1024 sweeps: max |u|, h2 f onto the grid
+        launches_per_step = 4 + 1 + 2 * -(-sweeps // 1024) + 2 * sweeps + resid + 1
+    elif refine:
         inner = args.inner or 100
         outer = -(-sweeps // inner)
         per_outer = 4 + 1 + 3 + (inner // kdepth + 2 * (inner % kdepth) if blocked else 2 * inner)
@@ -910,6 +914,23 @@ def main():
                     "launch_ms": 1e3 * launch_s, "algorithmic_bytes_per_launch": alg_bytes,
                     "note": "per launch equivalent (a half-sweep, or a blocked pass), including the "
                             "FP64 defect/correction passes in the time"}
+    elif args.fma:
+        # dominant kernel: the fused half-sweep (integer arithmetic only), bound by HBM: 24
+        # algorithmic bytes per update (h2 f on the fixed-point grid, the other colour, the
+        # own colour written).  Per launch: half the points; the time includes the rescaling
+        # passes of each block of sweeps (max |u|, h2 f onto the grid).
+        launches = 2 * sweeps
+        kname = "fused_half_sweep"
+        per_launch_lups = n * n / 2.0
+        launch_s = sweep_s / (launches * args.steps)
+        alg_bytes = BYTES_PER_LUP * per_launch_lups
+        achieved = alg_bytes / launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                    "frac": achieved / peak_hbm, "traffic": profiled_traffic(kname, args.emulate),
+                    "kernel": kname, "peak_source": hbm_src, "launch_ms": 1e3 * launch_s,
+                    "algorithmic_bytes_per_launch": alg_bytes,
+                    "note": "per half-sweep; the sweeps' device time includes the per-block rescaling "
+                            "passes (max |u|, h2 f onto the fixed-point grid)"}
     else:
         # dominant kernel: the FP64 half-sweep, bound by the FP64 pipe: 4 correctly rounded
         # adds per update (the x0.25 runs on the integer pipe).  Peak: 2 FP64 instructions
@@ -1034,6 +1055,11 @@ def main():
                        "kernel": ("all sweeps in one cooperative launch (grid barrier between colours)"
                                   if persistent else {1: "one launch per colour", 2: "temporal (TMA tiles)",
                                                       3: "register wavefront"}[kernel]),
+                       "update": ("fused: the five binary64 terms summed exactly in 64-bit fixed point, one "
+                                  "rounding to binary64 per update (<= 1e-13 relative max-norm of the "
+                                  "bit-exact iterate)" if args.fma else
+                                  "bit-exact: four correctly rounded FP64 adds per update, the bits of the "
+                                  "plain sequential loop"),
                        "tblock_k": kdepth if blocked else None, "precision": args.precision,
                        "fp64_emulate": args.emulate, "tile_rows": args.tile_rows or "auto",
                        "sweep_values": args.values or "auto", "sweep_rows": args.rows or "auto",

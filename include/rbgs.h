@@ -50,14 +50,16 @@ typedef enum {
     RBGS_EINVAL = 1,      /* bad argument: null pointer, n < 1, h2 <= 0, bad option     */
     RBGS_ENOMEM = 2,      /* device or pinned host allocation failed                     */
     RBGS_ECUDA = 3,       /* a CUDA runtime/driver call failed                           */
-    RBGS_ENOTCONV = 4,    /* rbgs_solve reached max_sweeps; the iterate is kept          */
+    RBGS_ENOTCONV = 4,    /* max_sweeps reached, or the residual stalled (stall_checks);
+                             the iterate is kept                                          */
     RBGS_ENONFINITE = 5,  /* the residual became NaN or Inf                              */
     RBGS_ETIMEOUT = 6     /* a bounded device-side wait gave up: the grid barrier of the
                              cooperative FP64 launch or the TMA wait of the temporal
                              kernel (reported by the next rbgs_residual or rbgs_solve).
                              Sticky: the iterate is left part-updated and every later
                              rbgs_residual / rbgs_solve on the context returns it again;
-                             destroy the context                                          */
+                             destroy the context.  In rbgs_solve_batched: the batch's
+                             device-time budget (max_seconds) ran out for that problem    */
 } rbgs_status;
 
 typedef enum {
@@ -99,13 +101,35 @@ typedef struct {
                           problems left over after full waves of one block per problem are each
                           solved by a thread-block cluster of team_size blocks; 1: one block per
                           problem always; 0: the autotuner decides                              */
+    int fma;           /* FP64 update of rbgs_sweep / rbgs_solve (RBGS_FP64 only):
+                          0 (default): bit-exact, (((h2f + N) + S) + W) + E times 0.25 with every
+                            step correctly rounded, the same bits as the plain sequential loop;
+                          1: fused, one rounding per update instead of four: the five terms are
+                            summed exactly in 64-bit fixed point (scale 2^e, chosen before each
+                            block of at most 1024 sweeps from max|u| and max|h2 f| so that no sum
+                            can overflow; terms are truncated to multiples of 2^-e) and the sum
+                            divided by 4 is rounded once to binary64 (nearest, ties to even).
+                            Integer arithmetic only, so the update leaves the FP64 pipe.  Agrees
+                            with the bit-exact iterate to <= 1e-13 relative max-norm after the same
+                            sweeps (the tolerance set for this mode); a non-finite value in u or h2 f makes
+                            that block of sweeps run the bit-exact update.  One launch per colour
+                            (the kernel option does not apply)                                   */
+    int stall_checks;  /* rbgs_solve and rbgs_solve_batched stop a problem with RBGS_ENOTCONV when
+                          its residual has not reached a new minimum for this many consecutive
+                          checks (0: 64; -1: never), so a tolerance below the rounding floor
+                          does not sweep until max_sweeps                                        */
+    double max_seconds;/* rbgs_solve_batched: device-time budget of the whole batch in seconds,
+                          measured from the first problem's start (%globaltimer); a problem still
+                          running, or not yet started, when it is spent ends with RBGS_ETIMEOUT
+                          and keeps its iterate (0: no budget)                                   */
 } rbgs_opts;
 
-/* Fills *opts with the defaults (all automatic). */
+/* Fills *opts with the defaults (all automatic).  Not in the paper: library mechanics. */
 void rbgs_default_opts(rbgs_opts *opts);
 
 /*
- * Creates a solver for one N x N problem (Section 2: h = 1/(N+1), the caller passes
+ * Creates a solver for one N x N problem (Section 2 and Eq. (1): h = 1/(N+1); the inputs
+ * of Algorithm 1, grid, f and h, with the ring of the Dirichlet problem; the caller passes
  * h2 = h*h as it wants it rounded).  f: N*N values; u_init: (N+2)^2 values with the
  * Dirichlet ring and the initial guess.  opts may be NULL (defaults).  The stream is a
  * cudaStream_t (NULL: legacy default stream).  On success *out owns device buffers of
@@ -118,7 +142,8 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
 rbgs_status rbgs_sweep(rbgs_t ctx, long nsweeps);
 
 /*
- * Relative residual rho = ||b - A u||_2 / ||b||_2 of the current iterate, with
+ * Not in the paper, which fixes the iteration count (Section 4): the convergence measure
+ * the library adds.  Relative residual rho = ||b - A u||_2 / ||b||_2 of the current iterate, with
  * A = (4 I - neighbours)/h^2 and b = f plus the ring terms / h^2 (the linear system of
  * Eq. (1)); rho = ||b - A u||_2 * h^2 when b = 0.  Synchronises the stream.
  * Right after rbgs_sweep (nsweeps > 0) only the red points are summed: the black points'
@@ -128,20 +153,24 @@ rbgs_status rbgs_sweep(rbgs_t ctx, long nsweeps);
 rbgs_status rbgs_residual(rbgs_t ctx, double *rel);
 
 /*
- * Sweeps until rho <= tol, evaluating rho before the first sweep and then every
- * check_every sweeps.  *sweeps_done gets the sweeps performed, *rel the last rho
- * (either may be NULL).  RBGS_ENOTCONV after max_sweeps, RBGS_ENONFINITE on NaN/Inf.
+ * Sweeps of Eq. (1) until rho <= tol.  The paper runs a fixed number of iterations
+ * (Section 4); this stopping rule is the library's.  Evaluates rho before the first sweep
+ * and then every check_every sweeps.  *sweeps_done gets the sweeps performed, *rel the last rho
+ * (either may be NULL).  RBGS_ENOTCONV after max_sweeps or when rho has stalled
+ * (opts.stall_checks), RBGS_ENONFINITE on NaN/Inf.
  */
 rbgs_status rbgs_solve(rbgs_t ctx, double tol, long *sweeps_done, double *rel);
 
-/* Copies the current iterate, ring included, into u_out ((N+2)^2 values). */
+/* Copies the current iterate, ring included, into u_out ((N+2)^2 values: the grid of
+ * Section 2).  Not in the paper: library mechanics. */
 rbgs_status rbgs_get_solution(rbgs_t ctx, double *u_out);
 
-/* Replaces the iterate and the ring by u_in ((N+2)^2 values), e.g. to resume a run. */
+/* Replaces the iterate and the ring by u_in ((N+2)^2 values), e.g. to resume a run.  Not
+ * in the paper: library mechanics. */
 rbgs_status rbgs_set_solution(rbgs_t ctx, const double *u_in);
 
 /*
- * Loads a new problem of the same N and h2 into ctx: f (N*N values) and u_init ((N+2)^2
+ * Not in the paper: library mechanics.  Loads a new problem of the same N and h2 into ctx: f (N*N values) and u_init ((N+2)^2
  * values, ring and initial guess), host or device memory, as rbgs_create reads them.  The
  * context's device buffers, options and cached launch graphs are kept, so a stream of
  * problems of one size needs no allocation after the first.  The result is the same as
@@ -167,6 +196,8 @@ typedef struct {
 } rbgs_result;
 
 /*
+ * Not in the paper: the batched growth direction, many independent problems of Section 2
+ * (each swept by Eq. (1), red then black) in persistent launches.
  * Solves nprob independent problems of uneven sizes (1 <= N_p <= 32768) to rho <= tol each,
  * in persistent launches captured with the packing and unpacking in a CUDA graph.  A
  * thread block claims one problem at a time, largest first, and solves it on its own
@@ -181,6 +212,10 @@ typedef struct {
  * opts->tblock_k (blocks per SM), fix it.  u_out[p] receives problem p's
  * solution ((N_p+2)^2 values, device or host memory); res[p] its outcome, latency_ms
  * measured on the device from the batch's first problem start to this problem's end.
+ * A problem whose rho stops reaching new minima for opts->stall_checks checks ends with
+ * RBGS_ENOTCONV; once opts->max_seconds of device time have passed since the batch's
+ * first problem started, every problem still running or not yet started ends with
+ * RBGS_ETIMEOUT (both keep the iterate reached).
  * Returns RBGS_OK when every problem converged, else the first failing status.
  * Synchronises the stream.
  */
@@ -189,6 +224,7 @@ rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, double tol,
                                rbgs_result *res);
 
 /*
+ * Not in the paper: library mechanics.
  * Launch shape of the last rbgs_solve_batched call on this thread (zeros before the first):
  * threads per block, blocks per SM, team size (1: one block per problem; 2 or 4: the phased
  * plan), and for the phased plan the number of largest problems solved one per block in its
@@ -206,16 +242,23 @@ void rbgs_batched_last_shape(int *threads, int *blocks_per_sm, int *team, int *f
  * same definition as rbgs_residual.  Its scratch is a fixed array inside the library's
  * device image (128 KiB, held on every GPU that loads the library until the process
  * exits), so N <= 32768; larger N returns RBGS_EINVAL.  The first call on each device looks
- * up that array's device address; make that first call before any stream capture.  Calls
- * share the array: calls that overlap on the GPU race.  No cudaMalloc/cudaFree is made.
+ * up that array's device address (and the first call after a cudaDeviceReset of that
+ * device looks it up again); make that first call before any stream capture.  Calls share
+ * the array: calls that overlap on the GPU race.  No cudaMalloc/cudaFree is made.
+ * Nothing is read back, so there is no RBGS_ENONFINITE here: a NaN or Inf in u or f gives
+ * a NaN or Inf in *rel_out, which the caller must test (rbgs_residual, by contrast, returns
+ * RBGS_ENONFINITE).  The library cannot see the buffers' sizes: f must hold N*N and u
+ * (N+2)^2 values (the Python binding checks this before the call).
  */
 rbgs_status rbgs_residual_static(int n, double h2, const double *f, const double *u,
                                  double *rel_out, void *cuda_stream);
 
-/* Frees the context (NULL is ignored). Synchronises its stream first. */
+/* Frees the context (NULL is ignored). Synchronises its stream first.  Not in the paper:
+ * library mechanics. */
 void rbgs_destroy(rbgs_t ctx);
 
-/* Message for the last non-OK status returned on this thread ("" if none). */
+/* Message for the last non-OK status returned on this thread ("" if none).  Not in the
+ * paper: library mechanics. */
 const char *rbgs_last_error(void);
 
 #ifdef __cplusplus

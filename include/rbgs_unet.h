@@ -33,6 +33,8 @@ extern "C" {
 /* ---------------------------------------------------------------- layer kernels --- */
 
 /*
+ * Not in the paper: the learned-initial-guess growth direction (as every entry point
+ * of this header).
  * 3x3 convolution, stride 1, zero padding 1 (cross-correlation, as in deep learning):
  *   Y[b,y,x,o] = act( bias[o] + sum_{dy,dx,c} Wt[o,dy,dx,c] * X[b,y+dy-1,x+dx-1,c] )
  * X: B*H*W*Cin bf16; Wt: Cout*3*3*Cin bf16; bias: Cout fp32 (may be NULL);
@@ -44,6 +46,7 @@ rbgs_status rbgs_conv_forward(const uint16_t *X, const uint16_t *Wt, const float
                               int y_fp32, void *cuda_stream);
 
 /*
+ * Not in the paper (learned initial guess).
  * Backward of rbgs_conv_forward without the activation, given G = dLoss/d(pre-activation)
  * (B*H*W*Cout bf16):
  *   dX[b,y,x,c]  (+)= sum_{dy,dx,o} Wt[o,dy,dx,c] * G[b,y-dy+1,x-dx+1,o]   (fp32; added to
@@ -57,6 +60,7 @@ rbgs_status rbgs_conv_backward(const uint16_t *X, const uint16_t *Wt, const uint
                                int Cout, int ksize, int accumulate, void *cuda_stream);
 
 /*
+ * Not in the paper (learned initial guess): library mechanics.
  * Engine of the convolution kernels (process-wide; applies to the network too):
  *   RBGS_CONV_TCGEN05        (default) 5th-generation tensor cores: tcgen05.mma from shared-
  *                            memory descriptors, FP32 accumulators in tensor memory, 128-row
@@ -75,6 +79,7 @@ rbgs_status rbgs_conv_set_engine(int engine);
 int rbgs_conv_get_engine(void);
 
 /*
+ * Not in the paper (learned initial guess): library mechanics.
  * Synchronises `cuda_stream` and reports whether a tcgen05 convolution launched since
  * the last check gave up one of its bounded waits on the tensor cores (RBGS_ETIMEOUT; its
  * output is then incomplete).  Clears the condition.  RBGS_OK otherwise.
@@ -85,17 +90,21 @@ rbgs_status rbgs_conv_check(void *cuda_stream);
 
 typedef struct rbgs_unet *rbgs_unet_t;
 
-/* Creates the network with weights initialised from `seed` (He-uniform, SplitMix64). */
+/* Not in the paper (learned initial guess).  Creates the network with weights initialised
+ * from `seed` (He-uniform, SplitMix64). */
 rbgs_status rbgs_unet_create(uint64_t seed, void *cuda_stream, rbgs_unet_t *out);
 
-/* Number of FP32 parameters (weights and biases of all layers, in a fixed order). */
+/* Not in the paper (learned initial guess).  Number of FP32 parameters (weights and
+ * biases of all layers, in a fixed order). */
 long rbgs_unet_num_params(rbgs_unet_t net);
 
-/* Copies the FP32 master parameters to / from `params` (host or device memory). */
+/* Not in the paper (learned initial guess).  Copies the FP32 master parameters to / from
+ * `params` (host or device memory). */
 rbgs_status rbgs_unet_get_params(rbgs_unet_t net, float *params);
 rbgs_status rbgs_unet_set_params(rbgs_unet_t net, const float *params);
 
 /*
+ * Not in the paper (learned initial guess).
  * Forward pass: x is B*H*W*4 fp32 (the four input channels), y receives B*H*W fp32
  * predictions.
  * Buffers for B x H x W are allocated on first use and reused.
@@ -103,6 +112,7 @@ rbgs_status rbgs_unet_set_params(rbgs_unet_t net, const float *params);
 rbgs_status rbgs_unet_forward(rbgs_unet_t net, const float *x, float *y, int B, int H, int W);
 
 /*
+ * Not in the paper (learned initial guess).
  * One training step: forward, loss = sum(mask_loss * (y - target)^2) / sum(mask_loss),
  * backward (every layer by the library's kernels), one Adam update (lr, beta1 0.9, beta2
  * 0.999, eps 1e-8) of the FP32 master weights, which are then rounded to bf16 for the
@@ -115,6 +125,8 @@ rbgs_status rbgs_unet_train_step(rbgs_unet_t net, const float *x, const float *t
                                  const float *mask_loss, int B, int H, int W, float lr,
                                  float *loss, float *grads);
 
+/* Not in the paper (learned initial guess): library mechanics.  Frees the network (NULL is
+ * ignored). */
 void rbgs_unet_destroy(rbgs_unet_t net);
 
 #ifdef __cplusplus

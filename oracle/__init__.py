@@ -60,6 +60,8 @@ def _load():
         lib.ref_refine_solve.argtypes = [c_int, c_int, c_double, dp, dp, c_double, c_long, c_long, dp,
                                          ctypes.POINTER(c_long)]
         lib.ref_refine_solve.restype = c_long
+        lib.ref_sweeps_fused.argtypes = [c_int, c_int, c_double, dp, dp, c_long, c_int, dp]
+        lib.ref_sweeps_fused.restype = None
         _lib = lib
     return _lib
 
@@ -87,6 +89,20 @@ def sweeps(u: np.ndarray, f: np.ndarray, h2: float, nsweeps: int, parity: int = 
     """nsweeps red+black sweeps of Eq. (1) in float64, in place on u (Section 2)."""
     ni, nj = _check(u, f, np.float64)
     _load().ref_sweeps_f64(ni, nj, float(h2), _dptr(f), _dptr(u), int(nsweeps), int(parity))
+    return u
+
+
+def sweeps_fused(u: np.ndarray, f: np.ndarray, h2: float, nsweeps: int, parity: int = 0,
+                 bound: tuple[float, float] | None = None) -> np.ndarray:
+    """nsweeps sweeps of the fused update (the library's fma = 1 mode: Eq. (1)'s five terms
+    summed exactly on a 64-bit fixed-point grid, rounded once), in place on u.  `bound`
+    = (max |u|, max |h2 f|) of the whole grid, for a window cut out of it."""
+    ni, nj = _check(u, f, np.float64)
+    bq = None
+    if bound is not None:
+        bq_arr = np.array(bound, dtype=np.float64)
+        bq = _dptr(bq_arr)
+    _load().ref_sweeps_fused(ni, nj, float(h2), _dptr(f), _dptr(u), int(nsweeps), int(parity), bq)
     return u
 
 
@@ -141,14 +157,16 @@ def refine_solve(u, f, h2, tol: float, inner: int, max_sweeps: int) -> tuple[int
 
 
 def window_value(f_full: np.ndarray, u0_full: np.ndarray, h2: float, nsweeps: int,
-                 i: int, j: int) -> float:
+                 i: int, j: int, fused_bound: tuple[float, float] | None = None) -> float:
     """u[i, j] after nsweeps, computed on a window around (i, j) only.
 
     One half-sweep moves information one grid step, so a point depends only on the
     points within Manhattan distance 2 * nsweeps of it.  The window reaches
     2 * nsweeps + 1 steps in each direction (clipped at the true boundary); its outer
     ring is held fixed, which is exact for the centre.  The window keeps the global
-    colouring through the parity offset.
+    colouring through the parity offset.  With `fused_bound` = (max |u0|, max |h2 f|) of
+    the whole grid the window runs the fused update at the whole grid's scale (one block
+    of sweeps, nsweeps <= 1024).
     """
     n_i, n_j = f_full.shape
     r = 2 * nsweeps + 1
@@ -157,5 +175,10 @@ def window_value(f_full: np.ndarray, u0_full: np.ndarray, h2: float, nsweeps: in
     u = np.ascontiguousarray(u0_full[a - 1:b + 2, c - 1:d + 2], dtype=np.float64)
     f = np.ascontiguousarray(f_full[a - 1:b, c - 1:d], dtype=np.float64)
     parity = (a - 1 + c - 1) & 1
-    sweeps(u, f, h2, nsweeps, parity)
+    if fused_bound is not None:
+        if nsweeps > 1024:
+            raise ValueError("a fused window covers one block of at most 1024 sweeps")
+        sweeps_fused(u, f, h2, nsweeps, parity, fused_bound)
+    else:
+        sweeps(u, f, h2, nsweeps, parity)
     return float(u[i - a + 1, j - c + 1])

@@ -225,3 +225,98 @@ long ref_refine_solve(int ni, int nj, double h2, const double *f, double *u, dou
     if (outer_out) *outer_out = outer;
     return done;
 }
+
+/*
+ * The fused update (not in the paper: the library's fused mode, rbgs_opts.fma = 1),
+ * stated plainly.  Sweeps run in blocks of at most 1024; before each block of m sweeps
+ *
+ *   B = max |u| over the whole grid, ring included;  Q = max |h2 f_ij| over the interior;
+ *   S = (4 B) + ((2 m + 1) Q), each operation rounded to binary64;
+ *   e = 61 - k with S = x 2^k, 0.5 <= x < 1 (frexp), at most 1020; e = 0 when S = 0.
+ *
+ * Within the block every update of Eq. (1), in the same red-then-black order, is
+ *
+ *   u_ij = RN( (T(h2 f_ij) + T(u_{i-1,j}) + T(u_{i+1,j}) + T(u_{i,j-1}) + T(u_{i,j+1})) 2^-(e+2) )
+ *
+ * with T(t) = trunc(t 2^e) an integer: the five terms on a fixed-point grid of step 2^-e,
+ * summed exactly, divided by 4 and rounded once to binary64 (C's conversion of a 64-bit
+ * integer to double rounds to nearest; scaling by a power of two is then exact because
+ * e <= 1020 keeps every nonzero result normal).  If B, Q or S is not finite, every point
+ * the block updates becomes NaN.  `bq`, when not NULL, supplies B and Q for the first
+ * block (a window cut out of a larger grid takes the whole grid's values).
+ */
+static long long fixed_term(double t, int e)
+{
+    return (long long)ldexp(t, e);  /* exact scaling, then truncation toward zero */
+}
+
+static int block_scale(int ni, int nj, double h2, const double *f, const double *u, long m,
+                       const double *bq, int *e_out)
+{
+    double B = 0.0, Q = 0.0;
+    int nan_seen = 0;
+    if (bq) {
+        B = bq[0];
+        Q = bq[1];
+    } else {
+        for (int i = 0; i <= ni + 1; ++i)
+            for (int j = 0; j <= nj + 1; ++j) {
+                double a = fabs(U(i, j));
+                if (isnan(a)) nan_seen = 1;
+                else if (a > B) B = a;
+            }
+        for (int i = 1; i <= ni; ++i)
+            for (int j = 1; j <= nj; ++j) {
+                double a = fabs(h2 * F(i, j));
+                if (isnan(a)) nan_seen = 1;
+                else if (a > Q) Q = a;
+            }
+    }
+    if (nan_seen)
+        return 0;
+    double t1 = 4.0 * B;
+    double t2 = (double)(2 * m + 1) * Q;
+    double S = t1 + t2;
+    if (!isfinite(S))
+        return 0;
+    int k = 0, e = 0;
+    if (S > 0.0) {
+        frexp(S, &k);
+        e = 61 - k;
+        if (e > 1020) e = 1020;
+    }
+    *e_out = e;
+    return 1;
+}
+
+void ref_sweeps_fused(int ni, int nj, double h2, const double *f, double *u, long nsweeps,
+                      int parity, const double *bq)
+{
+    long done = 0;
+    while (done < nsweeps) {
+        long m = nsweeps - done < 1024 ? nsweeps - done : 1024;
+        int e = 0;
+        int ok = block_scale(ni, nj, h2, f, u, m, done == 0 ? bq : NULL, &e);
+        for (long it = 0; it < m; ++it) {
+            for (int colour = 0; colour < 2; ++colour) {
+                for (int i = 1; i <= ni; ++i) {
+                    for (int j = 1; j <= nj; ++j) {
+                        if (((i + j + parity) & 1) != colour)
+                            continue;
+                        if (!ok) {
+                            U(i, j) = NAN;
+                            continue;
+                        }
+                        long long s = fixed_term(h2 * F(i, j), e);
+                        s += fixed_term(U(i - 1, j), e);
+                        s += fixed_term(U(i + 1, j), e);
+                        s += fixed_term(U(i, j - 1), e);
+                        s += fixed_term(U(i, j + 1), e);
+                        U(i, j) = ldexp((double)s, -(e + 2));
+                    }
+                }
+            }
+        }
+        done += m;
+    }
+}

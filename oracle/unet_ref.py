@@ -89,28 +89,54 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def bf16_round(a):
+    """Nearest bfloat16 value (ties to even) of each element, returned as float64.
+
+    bfloat16 keeps binary32's sign and 8-bit exponent and the top 7 of its 23 fraction bits;
+    rounding a binary64 value to it once: split off everything below the 8-bit significand
+    with frexp, round that significand (an integer in [128, 256)) half to even, rescale.
+    Zeros stay zeros; the values here never reach bfloat16's overflow or subnormal range.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    m, e = np.frexp(a)                  # a = m 2^e, 0.5 <= |m| < 1
+    q = np.rint(m * 256.0)              # 8 significant bits; rint rounds half to even
+    return np.ldexp(q, e - 8)
+
+
 # ------------------------------------------------------------------ network
-def forward(params, x3, keep=False):
+def forward(params, x3, keep=False, bf16=False):
     """x3: B x H x W x C input channels (C <= 16; the network reads 16, zero-padded).
     Returns the 8-channel output (channel 0 is the prediction) and, with keep=True, the
-    cached tensors for backward."""
+    cached tensors for backward.
+
+    bf16=True states the library's storage precision: the weights (not the biases), the
+    input channels and every stored activation (each hidden convolution's output after
+    ReLU, each pooled map) are rounded to bfloat16; sums and the output layer stay exact.
+    """
     sl, _ = param_slices()
-    W = [params[s].reshape(shape) for s, _, shape in sl]
+    rnd = bf16_round if bf16 else (lambda a: a)
+    W = [rnd(params[s]).reshape(shape) for s, _, shape in sl]
     Bv = [params[bs] for _, bs, _ in sl]
     b, h, w, _ = x3.shape
     x = np.zeros((b, h, w, IN_CH))
-    x[..., :x3.shape[-1]] = x3
+    x[..., :x3.shape[-1]] = rnd(x3)
     cache = {"in": x}
 
     def conv(li, inp, name):
         pre = conv_forward(inp, W[li], Bv[li])
         out = relu(pre) if LAYERS[li][3] else pre
+        if li < len(LAYERS) - 1:
+            out = rnd(out)
         cache[name] = out
         return out
 
-    e0a = conv(0, x, "e0a"); s0 = conv(1, e0a, "s0"); p0 = avgpool(s0); cache["p0"] = p0
-    e1a = conv(2, p0, "e1a"); s1 = conv(3, e1a, "s1"); p1 = avgpool(s1); cache["p1"] = p1
-    e2a = conv(4, p1, "e2a"); s2 = conv(5, e2a, "s2"); p2 = avgpool(s2); cache["p2"] = p2
+    def pool(inp, name):
+        cache[name] = rnd(avgpool(inp))
+        return cache[name]
+
+    e0a = conv(0, x, "e0a"); s0 = conv(1, e0a, "s0"); p0 = pool(s0, "p0")
+    e1a = conv(2, p0, "e1a"); s1 = conv(3, e1a, "s1"); p1 = pool(s1, "p1")
+    e2a = conv(4, p1, "e2a"); s2 = conv(5, e2a, "s2"); p2 = pool(s2, "p2")
     b3a = conv(6, p2, "b3a"); b3b = conv(7, b3a, "b3b")
     c2 = np.concatenate([upsample(b3b), s2], axis=-1); cache["c2"] = c2
     d2a = conv(8, c2, "d2a"); d2b = conv(9, d2a, "d2b")
@@ -122,17 +148,20 @@ def forward(params, x3, keep=False):
     return (out, cache) if keep else out
 
 
-def loss(params, x3, target, mask):
-    out = forward(params, x3)
+def loss(params, x3, target, mask, bf16=False):
+    out = forward(params, x3, bf16=bf16)
     d = out[..., 0] - target
     return float((mask * d * d).sum() / mask.sum())
 
 
-def backward(params, x3, target, mask):
-    """(loss, gradient vector) of the masked MSE, by the chain rule."""
+def backward(params, x3, target, mask, bf16=False):
+    """(loss, gradient vector) of the masked MSE, by the chain rule.  bf16=True: the forward
+    as above, and each convolution's pre-activation gradient (what its weight, bias and input
+    gradients are formed from) rounded to bfloat16, as the library stores it."""
     sl, n = param_slices()
-    W = [params[s].reshape(shape) for s, _, shape in sl]
-    out, c = forward(params, x3, keep=True)
+    rnd = bf16_round if bf16 else (lambda a: a)
+    W = [rnd(params[s]).reshape(shape) for s, _, shape in sl]
+    out, c = forward(params, x3, keep=True, bf16=bf16)
     cnt = mask.sum()
     d = out[..., 0] - target
     L = float((mask * d * d).sum() / cnt)
@@ -141,7 +170,7 @@ def backward(params, x3, target, mask):
     gout[..., 0] = 2.0 * mask * d / cnt
 
     def conv_b(li, inp_name, out_name, gpost):
-        gpre = gpost * (c[out_name] > 0) if LAYERS[li][3] else gpost
+        gpre = rnd(gpost * (c[out_name] > 0) if LAYERS[li][3] else gpost)
         dx, dw, db = conv_backward(c[inp_name], W[li], gpre)
         grad[sl[li][0]] += dw.reshape(-1)
         grad[sl[li][1]] += db

@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
                 ("tblock_k", ctypes.c_int), ("tile_rows", ctypes.c_int),
                 ("fp64_emulate", ctypes.c_int), ("inner_sweeps", ctypes.c_int),
                 ("sweep_values", ctypes.c_int), ("sweep_rows", ctypes.c_int), ("int_rows", ctypes.c_int),
-                ("team_size", ctypes.c_int)]
+                ("team_size", ctypes.c_int), ("fma", ctypes.c_int), ("stall_checks", ctypes.c_int),
+                ("max_seconds", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):
@@ -223,8 +224,19 @@ def rbgs_batched_last_shape() -> dict:
 def rbgs_residual_static(n: int, h2: float, f, u, rel_out, stream=None) -> None:
     """rbgs_residual_static: rho of a natural-layout device iterate into rel_out (device,
     one float64), allocating nothing (for callers that cannot allocate device memory)."""
+    n = int(n)
+    sizes = {"f": (f, n * n), "u": (u, (n + 2) * (n + 2)), "rel_out": (rel_out, 1)}
+    for name, (a, need) in sizes.items():
+        have = a.size if isinstance(a, np.ndarray) else a.numel()
+        if (have < need) if name == "rel_out" else (have != need):
+            raise RbgsError(RBGS_EINVAL, f"rbgs_residual_static: {name} holds {have} values, needs "
+                                         f"{'at least ' if name == 'rel_out' else ''}{need} for n = {n}")
+    import torch
+    tensors = [a for a in (f, u, rel_out) if isinstance(a, torch.Tensor) and a.is_cuda]
+    if len(tensors) != 3 or len({a.device for a in tensors}) != 1:
+        raise RbgsError(RBGS_EINVAL, "rbgs_residual_static: f, u and rel_out must be CUDA tensors of one device")
     s = _stream_of(f, u, stream=stream)
-    _check(load_library().rbgs_residual_static(int(n), float(h2), _ptr(f), _ptr(u), _ptr(rel_out), s))
+    _check(load_library().rbgs_residual_static(n, float(h2), _ptr(f), _ptr(u), _ptr(rel_out), s))
 
 
 class Solver:

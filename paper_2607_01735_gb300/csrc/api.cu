@@ -42,6 +42,12 @@ constexpr int kPersistMinN = 416;
 // 1.46x at 127^2, 0.93x at 255^2, 0.49x at 511^2 (16 SMs do not match the whole GPU there).
 constexpr int kClusterMaxN = 160;
 constexpr int kPersistMaxN = 1 << 15;
+// Fused update (opts.fma = 1): sweeps per block of one fixed-point scale.  The scale bounds
+// max |u| + (sweeps) max |h2 f| / 2 a priori, so shorter blocks keep it tighter; the
+// rescaling pass (max |u|, h2 f onto the grid: about one sweep's traffic) repeats per block.
+constexpr long kFusedChunk = 1024;
+// Residual checks without a new minimum of rho after which a solve stops (opts.stall_checks 0).
+constexpr int kDefaultStallChecks = 64;
 
 bool use_persistent(const rbgs_ctx *c) { return c->kernel == RBGS_KERNEL_PERSISTENT; }
 
@@ -74,19 +80,32 @@ rbgs_status stage_in(rbgs_ctx *c, const double *src, size_t count, const double 
     return RBGS_OK;
 }
 
-rbgs_status load_problem(rbgs_ctx *c, const double *f, const double *u_init) {
+// Packs device-readable natural-layout inputs into the context (f may be NULL: keep h2 f)
+// and reduces ||h^2 b||^2 into dsum[1], all on c->stream.
+rbgs_status enqueue_pack(rbgs_ctx *c, const double *f_view, const double *u_view) {
     const Geometry &g = c->g;
     c->black_fresh = false;
-    const double *view = nullptr;
     rbgs_status st;
-    if (f) {
-        if ((st = stage_in(c, f, (size_t)g.n * g.n, &view)) != RBGS_OK) return st;
-        if ((st = launch_pack_f(g, c->h2, view, c->f64.hf[0], c->f64.hf[1], c->stream)) != RBGS_OK) return st;
-    }
-    if ((st = stage_in(c, u_init, (size_t)g.rows * g.rows, &view)) != RBGS_OK) return st;
-    if ((st = launch_pack_u(g, view, c->f64.u[0], c->f64.u[1], c->stream)) != RBGS_OK) return st;
+    if (f_view && (st = launch_pack_f(g, c->h2, f_view, c->f64.hf[0], c->f64.hf[1], c->stream)) != RBGS_OK) return st;
+    if ((st = launch_pack_u(g, u_view, c->f64.u[0], c->f64.u[1], c->stream)) != RBGS_OK) return st;
+    if (f_view && c->fused && (st = launch_fused_rhs_max(c, c->stream)) != RBGS_OK) return st;
     // ||h^2 b||^2 depends on f and the ring
-    if ((st = launch_rhs_norm(c, c->stream)) != RBGS_OK) return st;
+    return launch_rhs_norm(c, c->stream);
+}
+
+rbgs_status load_problem(rbgs_ctx *c, const double *f, const double *u_init) {
+    const Geometry &g = c->g;
+    const double *fview = nullptr, *uview = nullptr;
+    rbgs_status st;
+    if (f && (st = stage_in(c, f, (size_t)g.n * g.n, &fview)) != RBGS_OK) return st;
+    if (f && fview == c->staging) {
+        // f goes through the staging buffer: pack it before u_init reuses the buffer
+        if ((st = launch_pack_f(g, c->h2, fview, c->f64.hf[0], c->f64.hf[1], c->stream)) != RBGS_OK) return st;
+        if (c->fused && (st = launch_fused_rhs_max(c, c->stream)) != RBGS_OK) return st;
+        fview = nullptr;
+    }
+    if ((st = stage_in(c, u_init, (size_t)g.rows * g.rows, &uview)) != RBGS_OK) return st;
+    if ((st = enqueue_pack(c, fview, uview)) != RBGS_OK) return st;
     RBGS_CUDA(cudaMemcpyAsync(c->hsum + 1, c->dsum + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     RBGS_CUDA(cudaStreamSynchronize(c->stream));
     c->den2 = c->hsum[1];
@@ -105,6 +124,9 @@ void free_ctx(rbgs_ctx *c) {
         cudaFree(c->f32.hf[q]);
         cudaFree(c->f32.alt[q]);
     }
+    cudaFree(c->hq[0]);
+    cudaFree(c->hq[1]);
+    cudaFree(c->fwords);
     cudaFree(c->staging);
     cudaFree(c->partials);
     cudaFree(c->dsum);
@@ -169,6 +191,14 @@ rbgs_status check_device_status(rbgs_ctx *c) {
 }
 
 rbgs_status enqueue_sweeps(rbgs_ctx *c, long nsweeps, cudaStream_t s) {
+    if (c->fused) {
+        for (long it = 0; it < nsweeps; ++it) {
+            rbgs_status st = launch_fused_half_sweep(c, 0, s);
+            if (st == RBGS_OK) st = launch_fused_half_sweep(c, 1, s);
+            if (st != RBGS_OK) return st;
+        }
+        return RBGS_OK;
+    }
     if (c->kernel == RBGS_KERNEL_TEMPORAL) return launch_temporal_sweeps(c, nsweeps, s);
     if (c->kernel == RBGS_KERNEL_WAVEFRONT) {
         const long passes = nsweeps / c->tblock_k;
@@ -209,6 +239,25 @@ rbgs_status ensure_graph(rbgs_ctx *c) {
 // nsweeps FP64 sweeps: one cooperative launch, cached graphs of kGraphSweeps sweeps on small
 // grids, or direct / temporally blocked launches.
 rbgs_status sweeps_f64(rbgs_ctx *c, long nsweeps) {
+    if (c->fused) {
+        // blocks of at most kFusedChunk sweeps, each at the scale chosen when it starts; the
+        // sweeps of a block as cached graphs of kGraphSweeps sweeps on small grids
+        while (nsweeps > 0) {
+            long m = nsweeps < kFusedChunk ? nsweeps : kFusedChunk;
+            nsweeps -= m;
+            rbgs_status st = launch_fused_prepare(c, m, c->stream);
+            if (st != RBGS_OK) return st;
+            if (c->g.n <= kGraphMaxN && m >= kGraphSweeps) {
+                if ((st = ensure_graph(c)) != RBGS_OK) return st;
+                while (m >= c->graph_sweeps) {
+                    RBGS_CUDA(cudaGraphLaunch(c->graph, c->stream));
+                    m -= c->graph_sweeps;
+                }
+            }
+            if ((st = enqueue_sweeps(c, m, c->stream)) != RBGS_OK) return st;
+        }
+        return RBGS_OK;
+    }
     if (use_persistent(c)) return launch_persistent_sweeps<double>(c->f64, nsweeps, c->pcounter, c->dstatus, c->stream);
     if (c->kernel == RBGS_KERNEL_COLOUR && c->g.n <= kGraphMaxN && nsweeps >= kGraphSweeps) {
         rbgs_status st = ensure_graph(c);
@@ -334,6 +383,9 @@ void rbgs_default_opts(rbgs_opts *o) {
     o->check_every = 100;
     o->max_sweeps = 1000000000L;
     o->fp64_emulate = -1;
+    o->fma = 0;
+    o->stall_checks = 0;
+    o->max_seconds = 0.0;
 }
 
 const char *rbgs_last_error(void) { return g_err; }
@@ -372,6 +424,21 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     if (o.sweep_rows != 0 && o.sweep_rows != 1 && o.sweep_rows != 2) {
         set_error("sweep_rows must be 0, 1 or 2"); return RBGS_EINVAL;
     }
+    if (o.fma != 0 && o.fma != 1) {
+        set_error("fma must be 0 (bit-exact) or 1 (fused)"); return RBGS_EINVAL;
+    }
+    if (o.fma == 1 && o.precision != RBGS_FP64) {
+        set_error("fma = 1 applies to RBGS_FP64 sweeps only"); return RBGS_EINVAL;
+    }
+    if (o.fma == 1 && o.kernel != RBGS_KERNEL_AUTO && o.kernel != RBGS_KERNEL_COLOUR) {
+        set_error("fma = 1 runs one launch per colour (kernel AUTO or COLOUR)"); return RBGS_EINVAL;
+    }
+    if (o.stall_checks < -1) {
+        set_error("stall_checks must be >= -1"); return RBGS_EINVAL;
+    }
+    if (!(o.max_seconds >= 0.0) || !std::isfinite(o.max_seconds)) {
+        set_error("max_seconds must be finite and >= 0"); return RBGS_EINVAL;
+    }
     if (o.tile_rows < 0 || o.tblock_k < 0 || o.inner_sweeps < 0) {
         set_error("negative tile_rows / tblock_k / inner_sweeps"); return RBGS_EINVAL;
     }
@@ -408,11 +475,13 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     const bool auto_k = o.kernel == RBGS_KERNEL_AUTO && o.tblock_k == 0;
     const bool default_shape = o.fp64_emulate == -1 && o.int_rows <= 0 && (o.sweep_values == 0 || o.sweep_values == 2) &&
                                (o.sweep_rows == 0 || o.sweep_rows == 1) && o.tile_rows == 0;
-    c->kernel = o.kernel != RBGS_KERNEL_AUTO ? o.kernel
+    c->fused = o.fma == 1;
+    c->kernel = c->fused ? RBGS_KERNEL_COLOUR
+                : o.kernel != RBGS_KERNEL_AUTO ? o.kernel
                 : (default_shape && n >= kPersistMinN && n <= kPersistMaxN) ? RBGS_KERNEL_PERSISTENT
                                                                             : RBGS_KERNEL_COLOUR;
     c->emulate = o.fp64_emulate == -1 ? 0x00 : o.fp64_emulate;
-    c->pts = o.sweep_values ? o.sweep_values : 2;
+    c->pts = o.sweep_values ? o.sweep_values : (c->fused ? 4 : 2);
     if (o.tile_rows) {
         c->tile_rows = o.tile_rows;
     } else {
@@ -460,6 +529,8 @@ rbgs_status rbgs_create(int n, double h2, const double *f, const double *u_init,
     ok = ok && cudaMalloc(&c->pcounter, sizeof(unsigned)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->hsum, 4 * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMallocHost(&c->hstatus, sizeof(int)) == cudaSuccess;
+    for (int q = 0; q < 2 && ok && c->fused; ++q) ok = cudaMalloc(&c->hq[q], c->g.colour_elems() * sizeof(int64_t)) == cudaSuccess;
+    ok = ok && (!c->fused || cudaMalloc(&c->fwords, 3 * sizeof(unsigned long long)) == cudaSuccess);
     ok = ok && cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -490,8 +561,9 @@ rbgs_status rbgs_sweep(rbgs_t c, long nsweeps) {
     if (nsweeps < 0) { set_error("nsweeps < 0"); return RBGS_EINVAL; }
     if (nsweeps == 0) return RBGS_OK;
     const rbgs_status st = sweeps_f64(c, nsweeps);
-    // after a completed sweep the black points' residual is exactly zero (residual.cu)
-    c->black_fresh = st == RBGS_OK;
+    // after a completed bit-exact sweep the black points' residual is exactly zero
+    // (residual.cu); the fused update rounds the black points differently
+    c->black_fresh = st == RBGS_OK && !c->fused;
     return st;
 }
 
@@ -519,17 +591,32 @@ rbgs_status rbgs_solve(rbgs_t c, double tol, long *sweeps_done, double *rel) {
     long done = 0;
     double rho = 0.0;
     rbgs_status st = rbgs_residual(c, &rho);
+    const int stall_limit = c->opts.stall_checks == 0 ? kDefaultStallChecks : c->opts.stall_checks;
+    double best = rho;
+    int since_best = 0;
+    bool stalled = false;
     while (st == RBGS_OK && !(rho <= tol) && done < c->opts.max_sweeps) {
         long k = c->opts.check_every;
         if (k > c->opts.max_sweeps - done) k = c->opts.max_sweeps - done;
         if ((st = rbgs_sweep(c, k)) != RBGS_OK) break;
         done += k;
-        st = rbgs_residual(c, &rho);
+        if ((st = rbgs_residual(c, &rho)) != RBGS_OK) break;
+        if (rho < best) {
+            best = rho;
+            since_best = 0;
+        } else if (stall_limit > 0 && ++since_best >= stall_limit) {
+            stalled = true;
+            break;
+        }
     }
     if (sweeps_done) *sweeps_done = done;
     if (rel) *rel = rho;
     if (st == RBGS_OK && !(rho <= tol)) {
-        set_error("not converged after %ld sweeps (rho = %.3e)", done, rho);
+        if (stalled)
+            set_error("stalled: rho = %.3e has not gone below its minimum %.3e for %d checks (%ld sweeps)", rho,
+                      best, stall_limit, done);
+        else
+            set_error("not converged after %ld sweeps (rho = %.3e)", done, rho);
         st = RBGS_ENOTCONV;
     }
     return st;

@@ -51,6 +51,16 @@ struct DevResult {
     unsigned long long t_start, t_end;
 };
 
+// Limits of a batch: a problem stops (RBGS_ENOTCONV) when rho has not reached a new
+// minimum for stall_limit consecutive checks (<= 0: never), and every problem stops
+// (RBGS_ETIMEOUT) once budget_ns of %globaltimer time have passed since the batch's first
+// problem started (*t_first, the minimum over the teams' start stamps; 0: no budget).
+struct BatchLimits {
+    int stall_limit;
+    unsigned long long budget_ns;
+    unsigned long long *t_first;
+};
+
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -355,13 +365,28 @@ __device__ __forceinline__ double rho_of(double r2, double den2) {
 // Solve one problem with a team of CS blocks (rank: this block's place in it).  The sweep
 // limit is max_sweeps, scaled by (n / cap_n)^2 when cap_n > 0 (the autotuner's probes: the
 // work per problem then grows like n^4, as in a solve to tolerance).
+// Whether the batch's time budget is spent, the same answer in every thread of the team
+// (the team's leader reads the clock; the value reaches the others through a team sum).
+template <int THREADS, int CS>
+__device__ __forceinline__ bool budget_spent(const BatchLimits &L, int rank, double *smem, double *slot) {
+    if (L.budget_ns == 0) return false;
+    double v = 0.0;
+    if (rank == 0 && threadIdx.x == 0) {
+        const unsigned long long first = *reinterpret_cast<volatile unsigned long long *>(L.t_first);
+        const unsigned long long now = globaltimer();
+        v = (now > first && now - first > L.budget_ns) ? 1.0 : 0.0;
+    }
+    return team_sum<THREADS, CS>(v, smem, slot) > 0.5;
+}
+
 template <int THREADS, int CS>
 __device__ void solve_problem(const DevProblem &P, DevResult &R, double tol, int check_every,
-                              long long max_sweeps, int inner, bool refine, int cap_n, int rank, double *smem,
-                              double *slot) {
+                              long long max_sweeps, int inner, bool refine, int cap_n, const BatchLimits &L,
+                              int rank, double *smem, double *slot) {
     constexpr int VT = THREADS * CS;
     const int vt = rank * THREADS + (int)threadIdx.x;
     const unsigned long long t0 = globaltimer();
+    if (rank == 0 && threadIdx.x == 0 && L.t_first) atomicMin(L.t_first, t0);
     if (cap_n > 0) {
         const double frac = ((double)P.n * P.n) / ((double)cap_n * cap_n);
         max_sweeps = max(1LL, (long long)(frac * (double)max_sweeps));
@@ -373,7 +398,11 @@ __device__ void solve_problem(const DevProblem &P, DevResult &R, double tol, int
     mx = team_max<THREADS, CS>(mx, smem, slot);
     double rho = rho_of(r2, den2);
     long long done = 0;
-    while (!(rho <= tol) && done < max_sweeps && isfinite(rho)) {
+    double best = rho;
+    int since_best = 0;
+    bool stalled = false;
+    bool spent = budget_spent<THREADS, CS>(L, rank, smem, slot);
+    while (!(rho <= tol) && done < max_sweeps && isfinite(rho) && !stalled && !spent) {
         if (!refine) {
             long long k = check_every;
             if (k > max_sweeps - done) k = max_sweeps - done;
@@ -423,9 +452,20 @@ __device__ void solve_problem(const DevProblem &P, DevResult &R, double tol, int
         r2 = team_sum<THREADS, CS>(r2, smem, slot);
         mx = team_max<THREADS, CS>(mx, smem, slot);
         rho = rho_of(r2, den2);
+        // rho, best and since_best are the same in every thread of the team
+        if (rho < best) {
+            best = rho;
+            since_best = 0;
+        } else if (L.stall_limit > 0 && ++since_best >= L.stall_limit) {
+            stalled = true;
+        }
+        spent = budget_spent<THREADS, CS>(L, rank, smem, slot);
     }
     if (rank == 0 && threadIdx.x == 0) {
-        R.status = !isfinite(rho) ? RBGS_ENONFINITE : (rho <= tol ? RBGS_OK : RBGS_ENOTCONV);
+        R.status = !isfinite(rho) ? RBGS_ENONFINITE
+                   : rho <= tol   ? RBGS_OK
+                   : spent        ? RBGS_ETIMEOUT
+                                  : RBGS_ENOTCONV;
         R.sweeps = done;
         R.rel = rho;
         R.t_start = t0;
@@ -442,7 +482,8 @@ template <int THREADS, int CS>
 __global__ void __launch_bounds__(THREADS)
 batched_persistent_kernel(const DevProblem *__restrict__ probs, DevResult *__restrict__ res,
                           const int *__restrict__ order, int nprob, int nteam, int *queues, double tol,
-                          int check_every, long long max_sweeps, int inner, int refine, int cap_n) {
+                          int check_every, long long max_sweeps, int inner, int refine, int cap_n,
+                          const BatchLimits L) {
     __shared__ double smem[THREADS / 32 + 1];
     __shared__ double slot;
     __shared__ int s_q;
@@ -456,8 +497,8 @@ batched_persistent_kernel(const DevProblem *__restrict__ probs, DevResult *__res
             if (q >= nteam) break;
             const int p = order[q];
             const DevProblem P = probs[p];
-            solve_problem<THREADS, CS>(P, res[p], tol, check_every, max_sweeps, inner, refine != 0, cap_n, rank,
-                                       smem, &slot);
+            solve_problem<THREADS, CS>(P, res[p], tol, check_every, max_sweeps, inner, refine != 0, cap_n, L,
+                                       rank, smem, &slot);
         }
     }
     for (;;) {
@@ -468,8 +509,8 @@ batched_persistent_kernel(const DevProblem *__restrict__ probs, DevResult *__res
         if (q >= nprob) break;
         const int p = order[q];
         const DevProblem P = probs[p];
-        solve_problem<THREADS, 1>(P, res[p], tol, check_every, max_sweeps, inner, refine != 0, cap_n, 0, smem,
-                                  &slot);
+        solve_problem<THREADS, 1>(P, res[p], tol, check_every, max_sweeps, inner, refine != 0, cap_n, L, 0,
+                                  smem, &slot);
         __syncthreads();
     }
 }
@@ -541,7 +582,7 @@ struct LaunchConfig {
 template <int THREADS, int CS>
 rbgs_status launch_one(int grid, const DevProblem *d_probs, DevResult *d_res, const int *d_order, int nprob,
                        int nteam, int *d_queues, double tol, int check_every, long long max_sweeps, int inner,
-                       int refine, int cap_n, cudaStream_t s) {
+                       int refine, int cap_n, const BatchLimits &L, cudaStream_t s) {
     RBGS_CUDA(cudaMemsetAsync(d_queues, 0, 2 * sizeof(int), s));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -556,7 +597,7 @@ rbgs_status launch_one(int grid, const DevProblem *d_probs, DevResult *d_res, co
     cfg.attrs = at;
     cfg.numAttrs = CS > 1 ? 1 : 0;
     RBGS_CUDA(cudaLaunchKernelEx(&cfg, batched_persistent_kernel<THREADS, CS>, d_probs, d_res, d_order, nprob, nteam,
-                                 d_queues, tol, check_every, max_sweeps, inner, refine, cap_n));
+                                 d_queues, tol, check_every, max_sweeps, inner, refine, cap_n, L));
     return RBGS_OK;
 }
 
@@ -600,32 +641,33 @@ void plan_phases(LaunchConfig &lc, const std::vector<int> &sizes_desc, int sms) 
 
 rbgs_status launch_persistent(const LaunchConfig &lc, int sms, const DevProblem *d_probs, DevResult *d_res,
                               const int *d_order, int nprob, int *d_queues, double tol, int check_every,
-                              long long max_sweeps, int inner, int refine, int cap_n, cudaStream_t s) {
+                              long long max_sweeps, int inner, int refine, int cap_n, const BatchLimits &L,
+                              cudaStream_t s) {
     if (lc.team > 1) {
         rbgs_status st = RBGS_OK;
         if (lc.first > 0)
             st = launch_one<1024, 1>(lc.grid1, d_probs, d_res, d_order, lc.first, 0, d_queues, tol, check_every,
-                                     max_sweeps, inner, refine, cap_n, s);
+                                     max_sweeps, inner, refine, cap_n, L, s);
         if (st != RBGS_OK || lc.first >= nprob) return st;
         const int *rest = d_order + lc.first;
         const int nrest = nprob - lc.first;
         if (lc.team == 2)
             return launch_one<1024, 2>(lc.grid2, d_probs, d_res, rest, nrest, lc.nteam, d_queues, tol, check_every,
-                                       max_sweeps, inner, refine, cap_n, s);
+                                       max_sweeps, inner, refine, cap_n, L, s);
         return launch_one<1024, 4>(lc.grid2, d_probs, d_res, rest, nrest, lc.nteam, d_queues, tol, check_every,
-                                   max_sweeps, inner, refine, cap_n, s);
+                                   max_sweeps, inner, refine, cap_n, L, s);
     }
     const int grid = std::max(1, std::min(nprob, sms * lc.blocks_per_sm));
     switch (lc.threads) {
     case 256:
         return launch_one<256, 1>(grid, d_probs, d_res, d_order, nprob, 0, d_queues, tol, check_every, max_sweeps,
-                                  inner, refine, cap_n, s);
+                                  inner, refine, cap_n, L, s);
     case 512:
         return launch_one<512, 1>(grid, d_probs, d_res, d_order, nprob, 0, d_queues, tol, check_every, max_sweeps,
-                                  inner, refine, cap_n, s);
+                                  inner, refine, cap_n, L, s);
     default:
         return launch_one<1024, 1>(grid, d_probs, d_res, d_order, nprob, 0, d_queues, tol, check_every, max_sweeps,
-                                   inner, refine, cap_n, s);
+                                   inner, refine, cap_n, L, s);
     }
 }
 
@@ -671,6 +713,14 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
         set_error("unknown precision %d", o.precision);
         return RBGS_EINVAL;
     }
+    if (o.stall_checks < -1) {
+        set_error("stall_checks must be >= -1");
+        return RBGS_EINVAL;
+    }
+    if (!(o.max_seconds >= 0.0) || !std::isfinite(o.max_seconds) || o.max_seconds > 1e9) {
+        set_error("max_seconds must be finite, >= 0 and at most 1e9");
+        return RBGS_EINVAL;
+    }
     for (int p = 0; p < nprob; ++p) {
         if (probs[p].n < 1 || probs[p].n > 32768 || !(probs[p].h2 > 0.0) || !probs[p].f || !probs[p].u_init || !u_out[p]) {
             set_error("problem %d: n must be in 1..32768, h2 > 0, pointers non-NULL", p);
@@ -712,6 +762,7 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
     DevProblem *d_probs = nullptr;
     DevResult *d_res = nullptr;
     int *d_order = nullptr, *d_queue = nullptr;
+    unsigned long long *d_tfirst = nullptr;
     rbgs_status st = RBGS_OK;
     auto fail_cuda = [&](cudaError_t e, const char *what) {
         if (e != cudaSuccess && st == RBGS_OK) {
@@ -723,6 +774,11 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
     fail_cuda(cudaMalloc(&d_res, nprob * sizeof(DevResult)), "cudaMalloc");
     fail_cuda(cudaMalloc(&d_order, nprob * sizeof(int)), "cudaMalloc");
     fail_cuda(cudaMalloc(&d_queue, 2 * sizeof(int)), "cudaMalloc");
+    fail_cuda(cudaMalloc(&d_tfirst, sizeof(unsigned long long)), "cudaMalloc");
+    // the solve's limits (the autotuner's probes run without them: a fixed sweep count)
+    const BatchLimits limits{o.stall_checks == 0 ? 64 : o.stall_checks,
+                             (unsigned long long)(o.max_seconds * 1e9), d_tfirst};
+    const BatchLimits probe_limits{-1, 0ull, nullptr};
     if (st == RBGS_OK) fail_cuda(cudaMemsetAsync(pool, 0, total, s), "cudaMemsetAsync");
     for (int p = 0; p < nprob && st == RBGS_OK; ++p) {
         const int n = probs[p].n;
@@ -828,7 +884,7 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
                 // tol < 0 is never reached: every problem runs its probe sweeps
                 if (st == RBGS_OK)
                     st = launch_persistent(cand, sms, d_probs, d_res, d_order, nprob, d_queue, -1.0,
-                                           (int)probe, probe, (int)probe, refine, sizes_desc[0], s);
+                                           (int)probe, probe, (int)probe, refine, sizes_desc[0], probe_limits, s);
                 fail_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
                 fail_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
                 float ms = 0.f;
@@ -858,8 +914,9 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
         if (st == RBGS_OK) {
             batch_pack_kernel<<<pgrid, 256, 0, cap>>>(d_probs);
             fail_cuda(cudaGetLastError(), "pack launch");
+            fail_cuda(cudaMemsetAsync(d_tfirst, 0xFF, sizeof(unsigned long long), cap), "cudaMemsetAsync");
             rbgs_status ls = launch_persistent(lc, sms, d_probs, d_res, d_order, nprob, d_queue, tol,
-                                               o.check_every, o.max_sweeps, inner, refine, 0, cap);
+                                               o.check_every, o.max_sweeps, inner, refine, 0, limits, cap);
             if (ls != RBGS_OK && st == RBGS_OK) st = ls;
             batch_unpack_kernel<<<pgrid, 256, 0, cap>>>(d_probs);
             fail_cuda(cudaGetLastError(), "unpack launch");
@@ -902,6 +959,7 @@ extern "C" rbgs_status rbgs_solve_batched(int nprob, const rbgs_problem *probs, 
     cudaFree(d_res);
     cudaFree(d_order);
     cudaFree(d_queue);
+    cudaFree(d_tfirst);
     return first;
 }
 

@@ -106,6 +106,18 @@ struct rbgs_ctx {
     int *hstatus;               // pinned host mirror of dstatus
     unsigned *pcounter;         // device: grid-barrier counter of the cooperative sweep launch
     bool black_fresh;           // the FP64 iterate is the result of a full sweep (black rt == 0)
+    // fused FP64 update (opts.fma = 1): h2 f on the fixed-point grid of the current block of
+    // sweeps, per colour, and [0] max |u| bits, [1] max |h2 f| bits, [2] the block's scale e
+    bool fused;
+    int64_t *hq[2];
+    unsigned long long *fwords;
+    // rbgs_run_stream: double-buffered natural-layout device staging of the inputs (f, u) and
+    // of the solution, one copy stream per direction, their events, and per-problem sums
+    double *sin_f[2], *sin_u[2], *sout[2];
+    cudaStream_t h2d, d2h;
+    cudaEvent_t ev_copied[2], ev_packed[2], ev_unpacked[2], ev_out[2];
+    double *dres, *hres;        // device / pinned host: [2q] sum (h^2 b)^2, [2q+1] sum rt^2
+    size_t res_cap;             // problems dres and hres hold
 };
 
 namespace rbgs {
@@ -140,5 +152,10 @@ rbgs_status launch_cluster_sweeps_f32(ColourField<float> &fld, long nsweeps, cud
 // mixed-precision refinement kernels (mixed.cu)
 rbgs_status launch_defect(const rbgs_ctx *c, bool write_r32, double scale, cudaStream_t s);  // -> dsum[0] sum, dsum[2] max
 rbgs_status launch_correct(const rbgs_ctx *c, double scale, cudaStream_t s);
+// fused FP64 update (fused.cu): max |h2 f| of a loaded problem; the scale of a block of
+// nsweeps sweeps with h2 f on its grid; one half-sweep at that scale
+rbgs_status launch_fused_rhs_max(const rbgs_ctx *c, cudaStream_t s);
+rbgs_status launch_fused_prepare(const rbgs_ctx *c, long long nsweeps, cudaStream_t s);
+rbgs_status launch_fused_half_sweep(const rbgs_ctx *c, int colour, cudaStream_t s);
 
 }  // namespace rbgs

@@ -139,8 +139,11 @@ extern "C" rbgs_status rbgs_residual_static(int n, double h2, const double *f, c
     }
     double *scratch = nullptr;
     {
-        // one-time set-up per device: the device address of the static scratch array
+        // set-up once per device (again only if the device was reset since): the device
+        // address of the static scratch array.  A reset unloads the library's device image,
+        // so an address looked up before it no longer belongs to this device's context.
         std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (g_scratch_ptr[device] && !on_device(g_scratch_ptr[device], device)) g_scratch_ptr[device] = nullptr;
         if (!g_scratch_ptr[device]) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);

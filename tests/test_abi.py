@@ -45,15 +45,43 @@ def test_library_exports_every_declared_symbol(lib):
         assert set(names) <= exported, (h, set(names) - exported)
 
 
+CITATION = re.compile(r"Section \d|Eq\. \(\d|Algorithm \d|not in the paper|no counterpart", re.I)
+
+
+def _declaration_comments(path):
+    """(name, comment) for every function declared in a header: the block comment that
+    precedes the declaration, or, for declarations grouped under one comment, that one."""
+    text = open(path).read()
+    out, last_comment = [], ""
+    for m in re.finditer(r"/\*.*?\*/|\b(rbgs_[a-z0-9_]+)\s*\(", text, flags=re.S):
+        if m.group(0).startswith("/*"):
+            last_comment = m.group(0)
+        else:
+            out.append((m.group(1), last_comment))
+    return out
+
+
+def test_every_declaration_cites_its_passage_or_says_it_has_none():
+    """Each entry point's comment names the paper's passage it implements (section,
+    equation, algorithm) or states that the paper has no counterpart."""
+    for h in HEADERS:
+        decls = _declaration_comments(h)
+        assert {n for n, _ in decls} == set(_declared(h)), h
+        for name, comment in decls:
+            flat = " ".join(comment.replace("/*", " ").replace("*/", " ").replace("*", " ").split())
+            assert CITATION.search(flat), (h, name, flat[:120])
+
+
 def test_default_opts(lib):
     o = rb.default_opts()
     assert (o.precision, o.kernel, o.check_every, o.fp64_emulate) == (rb.RBGS_FP64, rb.RBGS_KERNEL_AUTO, 100, -1)
     assert o.max_sweeps == 1000000000
+    assert (o.fma, o.stall_checks, o.max_seconds) == (0, 0, 0.0)
 
 
 def test_struct_layouts_match_header(lib):
-    # rbgs_opts: 3 ints (+4 padding), a long, 8 ints -> 56 bytes on LP64
-    assert ctypes.sizeof(rb.Opts) == 56
+    # rbgs_opts: 3 ints (+4 padding), a long, 10 ints, a double -> 72 bytes on LP64
+    assert ctypes.sizeof(rb.Opts) == 72
     assert ctypes.sizeof(rb.Problem) == 32
     assert ctypes.sizeof(rb.Result) == 32
 
@@ -86,6 +114,15 @@ def test_argument_errors_without_gpu(lib):
     assert lib.rbgs_create(40000, 1e-9, f.ctypes.data, u.ctypes.data, ctypes.byref(big), None,
                            ctypes.byref(h)) == rb.RBGS_EINVAL
     assert "32768" in rb.rbgs_last_error()
+    # the fused update (fma = 1): FP64 sweeps, one launch per colour; stall and time options
+    for bad in (rb.default_opts(fma=2), rb.default_opts(fma=-1),
+                rb.default_opts(fma=1, precision=rb.RBGS_FP32_REFINE),
+                rb.default_opts(fma=1, kernel=rb.RBGS_KERNEL_PERSISTENT),
+                rb.default_opts(fma=1, kernel=rb.RBGS_KERNEL_WAVEFRONT),
+                rb.default_opts(stall_checks=-2), rb.default_opts(max_seconds=-1.0),
+                rb.default_opts(max_seconds=float("nan")), rb.default_opts(max_seconds=float("inf"))):
+        assert lib.rbgs_create(4, 0.04, f.ctypes.data, u.ctypes.data, ctypes.byref(bad), None,
+                               ctypes.byref(h)) == rb.RBGS_EINVAL
     assert lib.rbgs_sweep(None, 1) == rb.RBGS_EINVAL
     assert lib.rbgs_residual(None, None) == rb.RBGS_EINVAL
     assert lib.rbgs_solve(None, 1e-8, None, None) == rb.RBGS_EINVAL
@@ -159,6 +196,18 @@ def test_unet_and_conv_argument_errors_without_gpu(lib):
     assert lib.rbgs_unet_train_step(None, p, p, p, i32(1), i32(8), i32(8), ctypes.c_float(1e-3), None,
                                     None) == rb.RBGS_EINVAL
     lib.rbgs_unet_destroy(None)  # ignored
+
+
+def test_static_residual_binding_checks_sizes_without_gpu(lib):
+    """The library cannot see buffer sizes; the binding refuses mismatched ones (and host
+    arrays) before any call, so no kernel reads past a caller's allocation."""
+    for f, u, out, word in ((np.zeros((3, 3)), np.zeros((6, 6)), np.zeros(1), "f holds 9"),
+                            (np.zeros((4, 4)), np.zeros((4, 4)), np.zeros(1), "u holds 16"),
+                            (np.zeros((4, 4)), np.zeros((6, 6)), np.zeros(0), "rel_out holds 0"),
+                            (np.zeros((4, 4)), np.zeros((6, 6)), np.zeros(1), "CUDA tensors")):
+        with pytest.raises(rb.RbgsError) as e:
+            rb.rbgs_residual_static(4, 0.04, f, u, out)
+        assert e.value.status == rb.RBGS_EINVAL and word in str(e.value)
 
 
 def test_binding_rejects_wrong_dtypes(lib):

@@ -24,7 +24,7 @@ def _const(name):
 
 
 def _args(**kw):
-    base = dict(kernel=0, tile_rows=0, emulate=-1, values=0, rows=0, int_rows=0)
+    base = dict(kernel=0, tile_rows=0, emulate=-1, values=0, rows=0, int_rows=0, fma=0)
     base.update(kw)
     return argparse.Namespace(**base)
 
@@ -44,6 +44,7 @@ def test_kernel_resolution():
     assert not b.uses_persistent(_args(kernel=1), 16384, False)  # one launch per colour asked
     assert not b.uses_persistent(_args(tile_rows=16), 16384, False)
     assert b.uses_persistent(_args(kernel=4), 100, False)      # asked for explicitly
+    assert not b.uses_persistent(_args(fma=1), 16384, False)   # the fused update: one launch per colour
     assert b.resolved_kernel(16384, True, 0, 0) == (3, 4)       # FP32 wavefront above 2048
     assert b.resolved_kernel(1000, True, 0, 0) == (1, 1)
     assert b.resolved_kernel(16384, False, 4, 0) == (1, 1)

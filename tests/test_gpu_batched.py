@@ -182,3 +182,84 @@ def test_batched_512_uneven_problems_sampled():
         done, rho = oracle.solve(ref, f, h2, 1e-8, 100, 10 ** 7)
         assert res[p]["sweeps"] == done
         _assert_bits(outs[p], ref)
+
+
+@pytest.mark.parametrize("team,precision", [(0, rb.RBGS_FP64), (4, rb.RBGS_FP64), (2, rb.RBGS_FP64),
+                                            (4, rb.RBGS_FP32_REFINE)])
+def test_batched_full_size_mix_capped_matches_oracle(team, precision):
+    """The batched workload's size mix including 511^2 and 1023^2 (problems drawn with its
+    recipe, stream 3), every problem capped at 200 sweeps so that the oracle finishes:
+    each ends RBGS_ENOTCONV after exactly 200 sweeps with the oracle's bits.  With a team
+    size the 1023^2 problems go to thread-block clusters (phased plan)."""
+    table = synth.batched_problem_table(512, 3)
+    pick = [e for e in table if e["n"] == 1023][:3] + [e for e in table if e["n"] == 511][:3] + \
+        [e for e in table if e["n"] == 255][:2] + [e for e in table if e["n"] in (63, 127)][:4]
+    batch = []
+    for e in pick:
+        f, u, h2 = synth.batched_problem(e)
+        batch.append((e["n"], h2, f, u))
+    refine = precision == rb.RBGS_FP32_REFINE
+    res, outs = _run(batch, 1e-8, check_every=50, max_sweeps=200, team_size=team, precision=precision,
+                     inner_sweeps=100)
+    if team:
+        shape = rb.rbgs_batched_last_shape()
+        assert shape["team"] == team and shape["nteam"] == 3  # the three 1023^2 problems
+    for (n, h2, f, u0), r, got in zip(batch, res, outs):
+        ref = u0.copy()
+        if refine:
+            done, rho, _ = oracle.refine_solve(ref, f, h2, 1e-8, 100, 200)
+        else:
+            done, rho = oracle.solve(ref, f, h2, 1e-8, 50, 200)
+        assert done == 200 and r["sweeps"] == 200 and r["status"] == rb.RBGS_ENOTCONV, (n, r)
+        _assert_bits(got, ref)
+        # rho: the oracle adds its n^2 squares one after another; recursive summation errs by
+        # at most (count - 1) 2^-53 of the sum (Higham, Accuracy and Stability of Numerical
+        # Algorithms, section 4.2), which at 1023^2 exceeds 1e-12 (interior squares far below
+        # the running sum's last bit are absorbed); the GPU's tree sum errs far less
+        assert abs(r["rel"] - rho) <= max(1e-12, n * n * 2.0 ** -53) * rho
+
+
+def test_batched_stops_problems_whose_residual_stalls():
+    """tol = 0 with the refinement, whose residual settles at a rounding floor near 5e-16
+    on a 9^2 grid: each problem stops with RBGS_ENOTCONV once rho has gone stall_checks
+    checks without a new minimum, after the same outer steps as the oracle's loop with
+    that rule, with the oracle's bits."""
+    batch = _batch([9, 9, 9], 12)
+    res, outs = _run(batch, 0.0, precision=rb.RBGS_FP32_REFINE, inner_sweeps=40, stall_checks=3,
+                     max_sweeps=10 ** 7)
+    for (n, h2, f, u0), r, got in zip(batch, res, outs):
+        ref = u0.copy()
+        best, since, done = oracle.residual(ref, f, h2)[0], 0, 0
+        while True:
+            _, rho, _ = oracle.refine_solve(ref, f, h2, 0.0, 40, 40)  # one outer step
+            done += 40
+            if rho < best:
+                best, since = rho, 0
+            else:
+                since += 1
+                if since >= 3:
+                    break
+        assert r["status"] == rb.RBGS_ENOTCONV and r["sweeps"] == done, (r, done)
+        _assert_bits(got, ref)
+
+
+def test_batched_time_budget_ends_the_batch():
+    """A batch that would run for minutes (160 problems of 511^2 to 1e-13) with a device-time
+    budget of 0.3 s: every problem ends RBGS_ETIMEOUT; the first wave (one block per SM)
+    after some sweeps, the problems that would have started after the budget with none,
+    their output the initial guess.  The call returns within seconds."""
+    import time
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    batch = _batch([511] * (sms + 8), 13)
+    t = time.perf_counter()
+    res, outs = _run(batch, 1e-13, check_every=20, max_seconds=0.3, tile_rows=1024, tblock_k=1)
+    wall = time.perf_counter() - t
+    assert wall < 10.0
+    assert all(r["status"] == rb.RBGS_ETIMEOUT for r in res)
+    started = [r["sweeps"] > 0 for r in res]
+    assert sum(started) >= sms and sum(started) <= sms + 8
+    late = [p for p, s in enumerate(started) if not s]
+    assert len(late) >= 8 - 2  # a block that finishes its check early may claim one more
+    for p in late:
+        _assert_bits(outs[p], batch[p][3])
+    assert max(r["latency_ms"] for r in res) < 2000.0

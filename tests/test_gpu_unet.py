@@ -4,8 +4,13 @@ network gains over starting red-black Gauss-Seidel from u0 = 0.
 
 Operands are bf16 on the GPU, so the oracle receives the same bf16-rounded inputs;
 single-layer results then differ only by FP32 accumulation order (tolerance 1e-4 of
-the result scale).  The whole network stores bf16 activations between layers, so its
-gradient is compared by direction (cosine >= 0.99) and norm (within 5%).
+the result scale).  The whole network stores bf16 activations and bf16 pre-activation
+gradients between layers; the oracle states the same roundings (unet_ref with
+bf16=True), so the forward output and every layer's weight and bias gradient are compared
+element by element.  What remains is FP32 accumulation order: an element whose value lies
+within that difference of a bf16 rounding boundary rounds to the neighbouring bf16 value
+on one side, and later layers carry such one-ulp steps along, so the tolerance is NET_TOL
+of the scale (the largest magnitude of the output, or of that layer's gradient block).
 """
 import numpy as np
 import pytest
@@ -122,29 +127,40 @@ def test_conv_engines_agree(B, H, W, Cin, Cout, k):
             assert float((a - b).abs().max()) <= 1e-5 * scale + 1e-6
 
 
+NET_TOL = 1e-3
+
+
+def _f32(a):
+    """The float32 values the GPU receives, as float64 for the oracle."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
 def test_network_gradient_matches_oracle(engine):
     from paper_2607_01735_gb300.unet import UNet
     net = UNet(seed=7)
-    params = net.get_params().cpu().double().numpy()
+    params = net.get_params().cpu().double().numpy()   # FP32 master weights, exact in float64
     rng = np.random.default_rng(5)
     B, H, W = 2, 16, 16
-    x3 = rng.normal(size=(B, H, W, 4))
-    target = rng.normal(size=(B, H, W)) * 0.1
+    x3 = _f32(rng.normal(size=(B, H, W, 4)))
+    target = _f32(rng.normal(size=(B, H, W)) * 0.1)
     mask = (rng.uniform(size=(B, H, W)) > 0.2).astype(np.float64)
-    # the GPU's forward consumes bf16 weights and inputs: give the oracle the same values
-    pb = torch.from_numpy(params).float().to(torch.bfloat16).double().numpy()
-    xb = torch.from_numpy(x3).float().to(torch.bfloat16).double().numpy()
-    L_ref, g_ref = U.backward(pb, xb, target, mask)
+    L_ref, g_ref = U.backward(params, x3, target, mask, bf16=True)
     grads = torch.empty(net.num_params, dtype=torch.float32, device="cuda")
     L = net.train_step(torch.from_numpy(x3).float().cuda(), torch.from_numpy(target).float().cuda(),
                        torch.from_numpy(mask).float().cuda(), lr=0.0, grads=grads)
     g = grads.cpu().double().numpy()
-    assert abs(L - L_ref) <= 2e-2 * L_ref
-    cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
-    assert cos >= 0.99, cos
-    assert abs(np.linalg.norm(g) / np.linalg.norm(g_ref) - 1) <= 0.05
-    # padded input channels carry no gradient
+    assert abs(L - L_ref) <= NET_TOL * L_ref, (L, L_ref)
+    # every layer's weights and biases, element by element at that block's own scale
     sl, _ = U.param_slices()
+    worst = []
+    for li, (ws, bs, _) in enumerate(sl):
+        for name, blk in (("w", ws), ("b", bs)):
+            scale = np.max(np.abs(g_ref[blk]))
+            err = np.max(np.abs(g[blk] - g_ref[blk]))
+            worst.append((err / scale, li, name))
+    worst.sort(reverse=True)
+    assert worst[0][0] <= NET_TOL, worst[:4]
+    # padded input channels carry no gradient
     w0 = g[sl[0][0]].reshape(32, 3, 3, 16)
     assert np.all(w0[..., 4:] == 0)
 
@@ -159,11 +175,12 @@ def test_training_reduces_loss_and_forward_matches_oracle():
     m = torch.ones((B, H, W), device="cuda")
     losses = [net.train_step(x, t, m, lr=3e-3) for _ in range(150)]
     assert losses[-1] < 0.3 * losses[0]
-    # forward of the trained net vs the oracle on the same (bf16-rounded) parameters
-    p = net.get_params().cpu().float().to(torch.bfloat16).double().numpy()
+    # forward of the trained net vs the oracle stating the same bf16 storage, element by element
+    p = net.get_params().cpu().double().numpy()
     y = net.forward(x).cpu().double().numpy()
-    y_ref = U.forward(p, x.cpu().float().to(torch.bfloat16).double().numpy())[..., 0]
-    assert np.max(np.abs(y - y_ref)) <= 5e-2 * np.max(np.abs(y_ref))
+    y_ref = U.forward(p, x.cpu().double().numpy(), bf16=True)[..., 0]
+    err = np.max(np.abs(y - y_ref)) / np.max(np.abs(y_ref))
+    assert err <= NET_TOL, err
 
 
 @pytest.mark.slow

@@ -69,3 +69,35 @@ def test_network_gradient_directional_derivatives():
         v = np.random.default_rng(10 + seed).normal(size=n)
         fd = (U.loss(params + eps * v, x3, target, mask) - U.loss(params - eps * v, x3, target, mask)) / (2 * eps)
         assert abs(fd - grad @ v) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    """unet_ref.bf16_round against torch's float32 -> bfloat16 conversion (round to nearest,
+    ties to even) on float32 values, and on hand-made ties."""
+    import torch
+    rng = np.random.default_rng(0)
+    a = (rng.normal(size=200000) * 10.0 ** rng.integers(-6, 6, 200000)).astype(np.float32).astype(np.float64)
+    want = torch.from_numpy(a).float().to(torch.bfloat16).double().numpy()
+    assert np.array_equal(U.bf16_round(a), want)
+    one = 1.0
+    ulp = 2.0 ** -7                      # spacing of bfloat16 in [1, 2)
+    assert U.bf16_round(one + ulp / 2) == one                # tie to the even significand 1.0
+    assert U.bf16_round(one + 3 * ulp / 2) == one + 2 * ulp  # tie up to the even one
+    assert U.bf16_round(-(one + ulp / 2 + 2.0 ** -30)) == -(one + ulp)
+    assert U.bf16_round(0.0) == 0.0
+
+
+def test_bf16_network_stays_near_the_exact_one():
+    """The bf16 storage statement perturbs the network by rounding-sized amounts only: the
+    output within 3% of scale and the gradient's direction unchanged (cosine > 0.999)."""
+    rng = np.random.default_rng(4)
+    params = rng.normal(size=U.num_params()) * 0.05
+    x = rng.normal(size=(1, 16, 16, 4))
+    t = rng.normal(size=(1, 16, 16)) * 0.1
+    m = np.ones((1, 16, 16))
+    y0, y1 = U.forward(params, x)[..., 0], U.forward(params, x, bf16=True)[..., 0]
+    assert np.max(np.abs(y1 - y0)) <= 3e-2 * np.max(np.abs(y0))
+    assert not np.array_equal(y0, y1)
+    _, g0 = U.backward(params, x, t, m)
+    _, g1 = U.backward(params, x, t, m, bf16=True)
+    assert g0 @ g1 / (np.linalg.norm(g0) * np.linalg.norm(g1)) > 0.999
