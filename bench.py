@@ -43,6 +43,9 @@ PROFILES = {
     "half_sweep_f64": ("profiles/half_sweep_f64_n16384.md",
                        ["paper_2607_01735_gb300/csrc/sweep.cu", "paper_2607_01735_gb300/csrc/sweep_impl.cuh",
                         "paper_2607_01735_gb300/csrc/fp64.cuh"]),
+    "fused_half_sweep": ("profiles/fused_half_sweep_f64_n16384.md",
+                         ["paper_2607_01735_gb300/csrc/fused.cu", "paper_2607_01735_gb300/csrc/fixed64.cuh",
+                          "paper_2607_01735_gb300/csrc/fp64.cuh", "paper_2607_01735_gb300/csrc/sweep_impl.cuh"]),
     "persistent_sweeps<double>": ("profiles/persistent_sweeps_f64_n16384.md",
                                   ["paper_2607_01735_gb300/csrc/persistent.cu",
                                    "paper_2607_01735_gb300/csrc/grid_barrier.cuh",
@@ -68,8 +71,9 @@ def parse():
     p.add_argument("--values", type=int, default=0, help="values per thread in a half-sweep (0 auto, 2, 4)")
     p.add_argument("--rows", type=int, default=0, help="rows per loop step in a half-sweep (0 auto, 1, 2)")
     p.add_argument("--int-rows", type=int, default=0, help="hybrid FP64: integer-pipe rows per strip pair")
-    p.add_argument("--fma", type=int, default=0, choices=[0, 1],
-                   help="FP64 update: 0 bit-exact, 1 fused (exact fixed-point sum, one rounding)")
+    p.add_argument("--fma", type=int, default=-1, choices=[-1, 0, 1],
+                   help="FP64 update: 0 bit-exact, 1 fused (exact fixed-point sum, one rounding); -1 (default): "
+                        "both, the fused form as the headline")
     p.add_argument("--kernel", type=int, default=0,
                    help="0 auto, 1 one launch per colour, 2 temporal (TMA tiles), 3 register wavefront, "
                         "4 all sweeps in one cooperative launch (FP64)")
@@ -797,13 +801,13 @@ def main():
     u0 = torch.zeros(n + 2, n + 2, dtype=torch.float64, device=dev)
     out = torch.empty_like(u0)
     refine = args.precision == "refine"
-    opts = rb.default_opts(fp64_emulate=args.emulate, tile_rows=args.tile_rows, kernel=args.kernel,
-                           sweep_values=args.values, sweep_rows=args.rows, int_rows=args.int_rows,
-                           tblock_k=args.tblock_k,
-                           precision=rb.RBGS_FP32_REFINE if refine else rb.RBGS_FP64,
-                           inner_sweeps=args.inner, max_sweeps=sweeps, fma=args.fma)
+    # FP64 update forms to time: both by default (the fused form is the headline, the
+    # bit-exact one beside it, measured in the same run), or the one --fma names
+    modes = [0] if refine else ([args.fma] if args.fma >= 0 else [1, 0])
     lib = rb.load_library()
     stream = torch.cuda.current_stream(dev)
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -811,212 +815,188 @@ def main():
             dist.barrier()
             torch.cuda.synchronize(dev)
 
-    sweep_events = []
+    def measure(fma):
+        """Time args.steps whole steps of one FP64 update form on one context; returns the
+        figures and the context (destroyed by the caller)."""
+        margs = argparse.Namespace(**vars(args))
+        margs.fma = fma
+        opts = rb.default_opts(fp64_emulate=args.emulate, tile_rows=args.tile_rows, kernel=args.kernel,
+                               sweep_values=args.values, sweep_rows=args.rows, int_rows=args.int_rows,
+                               tblock_k=args.tblock_k,
+                               precision=rb.RBGS_FP32_REFINE if refine else rb.RBGS_FP64,
+                               inner_sweeps=args.inner, max_sweeps=sweeps, fma=fma)
+        sweep_events = []
 
-    # Solver contexts (device buffers) are allocated once, before timing; every step loads
-    # its problem into one (the layout/staging step: copies and packing), sweeps, computes
-    # the residual and reads the solution back.
-    def start(ctx, fi, ui, cuda_stream, record=False):
-        rb.rbgs_set_problem(ctx, fi, ui)
-        run_sweeps(ctx, cuda_stream, record)
+        # The solver context (device buffers) is allocated once, before timing; every step
+        # loads its problem into it (the layout/staging step: copies and packing), sweeps,
+        # computes the residual and reads the solution back.
+        def run_sweeps(ctx, record=False):
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            if refine:
+                rb.rbgs_solve(ctx, 0.0, allow_not_converged=True)
+            else:
+                rb.rbgs_sweep(ctx, sweeps)
+            if record:
+                e1.record(stream)
+                sweep_events.append((e0, e1))
 
-    def run_sweeps(ctx, cuda_stream, record=False):
-        if record:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(cuda_stream)
-        if refine:
-            rb.rbgs_solve(ctx, 0.0, allow_not_converged=True)
+        ctx = rb.rbgs_create(n, h2, f, u0, opts, stream=stream.cuda_stream)
+
+        def step(fi, ui, uo, record=False):
+            rb.rbgs_set_problem(ctx, fi, ui)
+            run_sweeps(ctx, record)
+            rho = rb.rbgs_residual(ctx)
+            rb.rbgs_get_solution(ctx, uo)
+            return rho
+
+        kernel, kdepth = resolved_kernel(n, refine, args.kernel, args.tblock_k)
+        if fma:
+            kernel, kdepth = 1, 1
+        blocked = kernel in (2, 3)  # several sweeps per launch (TMA tiles or register wavefront)
+        persistent = uses_persistent(margs, n, refine)
+        # pack f, pack u, ||b|| (2), the sweeps, residual, unpack.  The residual after
+        # bit-exact FP64 sweeps walks the red points only (2 launches: the black rt is exactly
+        # zero), else both colours (3)
+        resid = 2 if sweeps > 0 and not fma else 3
+        if fma:  # + max |h2 f| at load; per block of <= 1024 sweeps: max |u|, h2 f onto the grid
+            launches_per_step = 4 + 1 + 2 * -(-sweeps // 1024) + 2 * sweeps + resid + 1
+        elif refine:
+            inner = args.inner or 100
+            outer = -(-sweeps // inner)
+            per_outer = 4 + 1 + 3 + (inner // kdepth + 2 * (inner % kdepth) if blocked else 2 * inner)
+            launches_per_step = 4 + 4 + outer * per_outer + 3 + 1
+        elif blocked:
+            launches_per_step = 4 + sweeps // kdepth + 2 * (sweeps % kdepth) + resid + 1
+        elif persistent:  # one cooperative launch runs all the sweeps (up to 2^20 per launch)
+            launches_per_step = 4 + -(-sweeps // (1 << 20)) + resid + 1
         else:
-            rb.rbgs_sweep(ctx, sweeps)
-        if record:
-            e1.record(cuda_stream)
-            sweep_events.append((e0, e1))
+            launches_per_step = 4 + 2 * sweeps + resid + 1
 
-    def finish(ctx, uo):
-        rho = rb.rbgs_residual(ctx)
-        rb.rbgs_get_solution(ctx, uo)
-        return rho
-
-    ctx_a = rb.rbgs_create(n, h2, f, u0, opts, stream=stream.cuda_stream)
-
-    def step(fi, ui, uo, record=False):
-        start(ctx_a, fi, ui, stream, record)
-        return finish(ctx_a, uo)
-
-    kernel, kdepth = resolved_kernel(n, refine, args.kernel, args.tblock_k)
-    blocked = kernel in (2, 3)  # several sweeps per launch (TMA tiles or register wavefront)
-    persistent = uses_persistent(args, n, refine)
-    # pack f, pack u, ||b|| (2), the sweeps, residual, unpack.  The residual after FP64
-    # sweeps walks the red points only (2 launches: the black rt is exactly zero), else both
-    # colours (3)
-    resid = 2 if sweeps > 0 and not args.fma else 3
-    if args.fma:  # + max |h2 f| at load; per block of <= 1024 sweeps: max |u|, h2 f onto the grid
-        launches_per_step = 4 + 1 + 2 * -(-sweeps // 1024) + 2 * sweeps + resid + 1
-    elif refine:
-        inner = args.inner or 100
-        outer = -(-sweeps // inner)
-        per_outer = 4 + 1 + 3 + (inner // kdepth + 2 * (inner % kdepth) if blocked else 2 * inner)
-        launches_per_step = 4 + 4 + outer * per_outer + 3 + 1
-    elif blocked:
-        launches_per_step = 4 + sweeps // kdepth + 2 * (sweeps % kdepth) + resid + 1
-    elif persistent:  # one cooperative launch runs all the sweeps (up to 2^20 per launch)
-        launches_per_step = 4 + -(-sweeps // (1 << 20)) + resid + 1
-    else:
-        launches_per_step = 4 + 2 * sweeps + resid + 1
-
-    for _ in range(args.warmup):
-        step(f, u0, out)
-    barrier()
-    props = torch.cuda.get_device_properties(dev)
-    uuid = getattr(props, "uuid", None)
-    with ClockSampler(str(uuid) if uuid else None) as clocks:
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        marks = []
-        for _ in range(args.steps):
-            rho = step(f, u0, out, record=True)
-            marks.append(torch.cuda.Event(enable_timing=True))
-            marks[-1].record(stream)
-        t1.record(stream)
+        for _ in range(args.warmup):
+            step(f, u0, out)
         barrier()
-    elapsed = t0.elapsed_time(t1) / 1e3
-    step_ms = [a.elapsed_time(b) for a, b in zip([t0] + marks[:-1], marks)]
-    sweep_ms = [a.elapsed_time(b) for a, b in sweep_events]
-    if world > 1:
-        tt = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
-    lups = float(n) * n * sweeps * args.steps * world
-    value = lups / elapsed / 1e9
-    sweep_s = sum(a.elapsed_time(b) for a, b in sweep_events) / 1e3
-    peaks = measured_peaks()
-    peak_hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0)) if peaks else 2070.0
-    names = {2: "temporal_tile", 3: "wavefront_kernel"}
-    if refine:
-        # dominant kernel: the FP32 inner sweeps (12 algorithmic bytes per update for one
-        # launch per colour; a blocked pass moves the same bytes for kdepth sweeps)
-        kname = f"{names[kernel]}<float, {kdepth}>" if blocked else "half_sweep_f32"
-        if blocked:  # one pass: kdepth sweeps of every point, the iterate and h2f moved once
-            launches = max(sweeps // kdepth, 1)
-            per_launch_lups = float(n) * n * kdepth
-            alg_bytes = 12.0 * n * n
-        else:  # one half-sweep: half the points
+        with ClockSampler(str(uuid) if uuid else None) as clocks:
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            marks = []
+            for _ in range(args.steps):
+                rho = step(f, u0, out, record=True)
+                marks.append(torch.cuda.Event(enable_timing=True))
+                marks[-1].record(stream)
+            t1.record(stream)
+            barrier()
+        elapsed = t0.elapsed_time(t1) / 1e3
+        step_ms = [a.elapsed_time(b) for a, b in zip([t0] + marks[:-1], marks)]
+        sweep_ms = [a.elapsed_time(b) for a, b in sweep_events]
+        if world > 1:
+            tt = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            elapsed = float(tt.item())
+        lups = float(n) * n * sweeps * args.steps * world
+        sweep_s = sum(a.elapsed_time(b) for a, b in sweep_events) / 1e3
+        peaks = measured_peaks()
+        peak_hbm = peaks["hbm_gbs"] if peaks else 6800.0
+        hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+        sm_count = props.multi_processor_count
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0)) if peaks else 2070.0
+        names = {2: "temporal_tile", 3: "wavefront_kernel"}
+        if refine:
+            # dominant kernel: the FP32 inner sweeps (12 algorithmic bytes per update for one
+            # launch per colour; a blocked pass moves the same bytes for kdepth sweeps)
+            kname = f"{names[kernel]}<float, {kdepth}>" if blocked else "half_sweep_f32"
+            if blocked:  # one pass: kdepth sweeps of every point, the iterate and h2f moved once
+                launches = max(sweeps // kdepth, 1)
+                alg_bytes = 12.0 * n * n
+            else:  # one half-sweep: half the points
+                launches = 2 * sweeps
+                alg_bytes = 12 * n * n / 2.0
+            launch_s = sweep_s / (launches * args.steps)
+            achieved = alg_bytes / launch_s / 1e9
+            roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                        "frac": achieved / peak_hbm, "traffic": None, "kernel": kname, "peak_source": hbm_src,
+                        "launch_ms": 1e3 * launch_s, "algorithmic_bytes_per_launch": alg_bytes,
+                        "note": "per launch equivalent (a half-sweep, or a blocked pass), including the "
+                                "FP64 defect/correction passes in the time"}
+        elif fma:
+            # dominant kernel: the fused half-sweep (integer arithmetic only), bound by HBM: 24
+            # algorithmic bytes per update (h2 f on the fixed-point grid, the other colour, the
+            # own colour written).  Per launch: half the points; the time includes the
+            # rescaling passes of each block of sweeps (max |u|, h2 f onto the grid).
             launches = 2 * sweeps
-            per_launch_lups = n * n / 2.0
-            alg_bytes = 12 * per_launch_lups
-        launch_s = sweep_s / (launches * args.steps)
-        achieved = alg_bytes / launch_s / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
-                    "frac": achieved / peak_hbm, "traffic": None, "kernel": kname, "peak_source": hbm_src,
-                    "launch_ms": 1e3 * launch_s, "algorithmic_bytes_per_launch": alg_bytes,
-                    "note": "per launch equivalent (a half-sweep, or a blocked pass), including the "
-                            "FP64 defect/correction passes in the time"}
-    elif args.fma:
-        # dominant kernel: the fused half-sweep (integer arithmetic only), bound by HBM: 24
-        # algorithmic bytes per update (h2 f on the fixed-point grid, the other colour, the
-        # own colour written).  Per launch: half the points; the time includes the rescaling
-        # passes of each block of sweeps (max |u|, h2 f onto the grid).
-        launches = 2 * sweeps
-        kname = "fused_half_sweep"
-        per_launch_lups = n * n / 2.0
-        launch_s = sweep_s / (launches * args.steps)
-        alg_bytes = BYTES_PER_LUP * per_launch_lups
-        achieved = alg_bytes / launch_s / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
-                    "frac": achieved / peak_hbm, "traffic": profiled_traffic(kname, args.emulate),
-                    "kernel": kname, "peak_source": hbm_src, "launch_ms": 1e3 * launch_s,
-                    "algorithmic_bytes_per_launch": alg_bytes,
-                    "note": "per half-sweep; the sweeps' device time includes the per-block rescaling "
-                            "passes (max |u|, h2 f onto the fixed-point grid)"}
-    else:
-        # dominant kernel: the FP64 half-sweep, bound by the FP64 pipe: 4 correctly rounded
-        # adds per update (the x0.25 runs on the integer pipe).  Peak: 2 FP64 instructions
-        # per clock per SM (ncu's DFMA peak_sustained) x SMs x maximum SM clock.
-        # (the persistent kernel: per half-sweep equivalent, its launch time / (2 sweeps))
-        launches = (sweeps // kdepth) if blocked else 2 * sweeps
-        kname = (f"{names[kernel]}<double, {kdepth}>" if blocked
-                 else "persistent_sweeps<double>" if persistent else "half_sweep_f64")
-        per_launch_lups = n * n * sweeps / launches
-        launch_s = sweep_s / (launches * args.steps)
-        fp64_ops = 4 * per_launch_lups
-        achieved = fp64_ops / launch_s / 1e12
-        peak_alu = 2.0 * sm_count * sm_mhz * 1e6 / 1e12
-        alg_bytes = BYTES_PER_LUP * per_launch_lups
-        hbm_achieved = alg_bytes / launch_s / 1e9
-        traffic = None if blocked else profiled_traffic(kname, args.emulate)
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                    "frac": achieved / peak_alu, "traffic": traffic, "kernel": kname,
-                    "peak_source": f"FP64 pipe: 2 instr/clk/SM x {sm_count} SMs x {sm_mhz:.0f} MHz "
-                                   "(one flop = one correctly rounded FP64 add)",
-                    "launch_ms": 1e3 * launch_s, "algorithmic_bytes_per_launch": alg_bytes,
-                    "hbm": {"achieved": hbm_achieved, "peak": peak_hbm, "unit": "GB/s",
-                            "frac": hbm_achieved / peak_hbm, "peak_source": hbm_src}}
-        if persistent:
-            roofline["note"] = ("one cooperative launch runs all sweeps; launch_ms, traffic and the algorithmic "
-                                "bytes are per half-sweep equivalent (the launch / 2 sweeps)")
+            kname = "fused_half_sweep"
+            launch_s = sweep_s / (launches * args.steps)
+            alg_bytes = BYTES_PER_LUP * n * n / 2.0
+            achieved = alg_bytes / launch_s / 1e9
+            roofline = {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                        "frac": achieved / peak_hbm, "traffic": profiled_traffic(kname, args.emulate),
+                        "kernel": kname, "peak_source": hbm_src, "launch_ms": 1e3 * launch_s,
+                        "algorithmic_bytes_per_launch": alg_bytes,
+                        "note": "per half-sweep; the sweeps' device time includes the per-block rescaling "
+                                "passes (max |u|, h2 f onto the fixed-point grid)"}
+        else:
+            # dominant kernel: the FP64 half-sweep, bound by the FP64 pipe: 4 correctly rounded
+            # adds per update (the x0.25 runs on the integer pipe).  Peak: 2 FP64 instructions
+            # per clock per SM (ncu's DFMA peak_sustained) x SMs x maximum SM clock.
+            # (the persistent kernel: per half-sweep equivalent, its launch time / (2 sweeps))
+            launches = (sweeps // kdepth) if blocked else 2 * sweeps
+            kname = (f"{names[kernel]}<double, {kdepth}>" if blocked
+                     else "persistent_sweeps<double>" if persistent else "half_sweep_f64")
+            per_launch_lups = n * n * sweeps / launches
+            launch_s = sweep_s / (launches * args.steps)
+            achieved = 4 * per_launch_lups / launch_s / 1e12
+            peak_alu = 2.0 * sm_count * sm_mhz * 1e6 / 1e12
+            alg_bytes = BYTES_PER_LUP * per_launch_lups
+            hbm_achieved = alg_bytes / launch_s / 1e9
+            traffic = None if blocked else profiled_traffic(kname, args.emulate)
+            roofline = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                        "frac": achieved / peak_alu, "traffic": traffic, "kernel": kname,
+                        "peak_source": f"FP64 pipe: 2 instr/clk/SM x {sm_count} SMs x {sm_mhz:.0f} MHz "
+                                       "(one flop = one correctly rounded FP64 add)",
+                        "launch_ms": 1e3 * launch_s, "algorithmic_bytes_per_launch": alg_bytes,
+                        "hbm": {"achieved": hbm_achieved, "peak": peak_hbm, "unit": "GB/s",
+                                "frac": hbm_achieved / peak_hbm, "peak_source": hbm_src}}
+            if persistent:
+                roofline["note"] = ("one cooperative launch runs all sweeps; launch_ms, traffic and the "
+                                    "algorithmic bytes are per half-sweep equivalent (the launch / 2 sweeps)")
+        kdesc = ("all sweeps in one cooperative launch (grid barrier between colours)" if persistent
+                 else {1: "one launch per colour", 2: "temporal (TMA tiles)", 3: "register wavefront"}[kernel])
+        return {"ctx": ctx, "step": step, "value": lups / elapsed / 1e9, "elapsed": elapsed, "lups": lups,
+                "step_ms": step_ms, "sweep_ms": sweep_ms, "roofline": roofline, "clocks": clocks.summary(),
+                "rho": rho, "launches": launches_per_step * args.steps, "kernel": kdesc,
+                "blocked": blocked, "kdepth": kdepth}
+
+    results = {}
+    for fma in modes:
+        results[fma] = measure(fma)
+        if fma != modes[0]:
+            rb.rbgs_destroy(results[fma].pop("ctx"))
+    head = results[modes[0]]
+    ctx_a, step, lups, elapsed = head["ctx"], head["step"], head["lups"], head["elapsed"]
+    value = head["value"]
 
     e2e = None
     if not args.no_e2e:
-        # End to end from pinned host memory: every step copies its f and u0 in from pinned
-        # host buffers, solves, and copies the solution and rho out.  As a serving loop runs
-        # a stream of solves, the copies go on copy streams into device buffers (double
-        # buffered) while the previous or next step's sweeps run; the library then loads from
-        # and unpacks to device memory.  The serial figure beside it passes the host buffers
-        # to the library directly, one step after another, nothing overlapped.
+        # End to end from pinned host memory through the library's host path: every step
+        # copies its f and u0 in from page-locked host buffers, sweeps, and copies the
+        # solution and rho out.  rbgs_run_stream runs the steps as a stream of problems, its
+        # own copy streams moving the next step's inputs and the last step's solution while
+        # the current step sweeps.  The serial figure beside it passes the host buffers to
+        # rbgs_set_problem / rbgs_get_solution one step after another, nothing overlapped.
+        # (The refinement runs the serial form only.)
         fh = f.cpu().pin_memory()
         uh = u0.cpu().pin_memory()
         oh = torch.empty(n + 2, n + 2, dtype=torch.float64).pin_memory()
-        # one stream per direction: host-to-device and device-to-host copies use separate
-        # copy engines and link directions, so the next inputs and the last solution move
-        # at the same time
-        in_stream, out_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        d_in = [(torch.empty_like(f), torch.empty_like(u0)) for _ in range(2)]
-        d_out = [torch.empty_like(u0) for _ in range(2)]
 
-        def pipelined(k):
-            ev_in = [torch.cuda.Event(), torch.cuda.Event()]
-            ev_out = [None, None]
-            with torch.cuda.stream(in_stream):
-                d_in[0][0].copy_(fh, non_blocking=True)
-                d_in[0][1].copy_(uh, non_blocking=True)
-                ev_in[0].record(in_stream)
-            for i in range(k):
-                b = i % 2
-                stream.wait_event(ev_in[b])
-                rb.rbgs_set_problem(ctx_a, d_in[b][0], d_in[b][1])
-                if i + 1 < k:  # the next step's inputs, during this step's sweeps
-                    nb = 1 - b
-                    with torch.cuda.stream(in_stream):
-                        d_in[nb][0].copy_(fh, non_blocking=True)
-                        d_in[nb][1].copy_(uh, non_blocking=True)
-                        ev_in[nb].record(in_stream)
-                run_sweeps(ctx_a, stream)
-                rb.rbgs_residual(ctx_a)
-                if ev_out[b] is not None:
-                    stream.wait_event(ev_out[b])  # d_out[b]'s previous copy-out has finished
-                rb.rbgs_get_solution(ctx_a, d_out[b])
-                ready = torch.cuda.Event()
-                ready.record(stream)
-                with torch.cuda.stream(out_stream):
-                    out_stream.wait_event(ready)
-                    oh.copy_(d_out[b], non_blocking=True)  # during the next step's sweeps
-                    ev_out[b] = torch.cuda.Event()
-                    ev_out[b].record(out_stream)
+        def streamed(k):
+            rb.rbgs_run_stream(ctx_a, [fh] * k, [uh] * k, sweeps, [oh] * k)
 
         def timed(body):
             with ClockSampler(str(uuid) if uuid else None) as clk:
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                in_stream.wait_event(e0)
-                out_stream.wait_event(e0)
                 body()
-                for cs in (in_stream, out_stream):
-                    j = torch.cuda.Event()
-                    j.record(cs)
-                    stream.wait_event(j)
                 e1.record(stream)
                 barrier()
             et = e0.elapsed_time(e1) / 1e3
@@ -1026,17 +1006,22 @@ def main():
                 et = float(tt.item())
             return et, clk.summary()
 
-        pipelined(2)  # warm the host path
-        step(fh, uh, oh)
+        step(fh, uh, oh)  # warm the host path
+        if not refine:
+            streamed(2)
         barrier()
-        et, e2e_clocks = timed(lambda: pipelined(args.steps))
-        et_serial, _ = timed(lambda: [step(fh, uh, oh) for _ in range(args.steps)])
+        et_serial, serial_clocks = timed(lambda: [step(fh, uh, oh) for _ in range(args.steps)])
+        if refine:
+            et, e2e_clocks, how = et_serial, serial_clocks, "serial host calls (the refinement)"
+        else:
+            et, e2e_clocks = timed(lambda: streamed(args.steps))
+            how = ("rbgs_run_stream: the library's copy streams (one per direction) move the next step's "
+                   "inputs and the last step's solution through double-buffered device staging while the "
+                   "current step sweeps")
         e2e = {"value": lups / et / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 8 * (n * n + (n + 2) * (n + 2)),
                "d2h_bytes_per_step": 8 * (n + 2) * (n + 2) + 8,
-               "ms_per_step": 1e3 * et / args.steps, "clocks": e2e_clocks,
-               "pipelined": "host copies on two copy streams (one per direction) into double-buffered device "
-                            "inputs and out of the device solution, overlapping the neighbouring steps' sweeps",
+               "ms_per_step": 1e3 * et / args.steps, "clocks": e2e_clocks, "api": how,
                "serial": {"value": lups / et_serial / 1e9, "ms_per_step": 1e3 * et_serial / args.steps}}
     rb.rbgs_destroy(ctx_a)
 
@@ -1046,39 +1031,48 @@ def main():
             cpu = cpu_oracle_rate(n)
         ttr = None if args.no_ttr else time_to_residual(args.ttr_n)
         small = None if args.no_ttr else small_grid_history()
+        def update_desc(fma):
+            return ("fused: the five binary64 terms summed exactly in 64-bit fixed point, one rounding to "
+                    "binary64 per update (<= 1e-13 relative max-norm of the bit-exact iterate)" if fma else
+                    "bit-exact: four correctly rounded FP64 adds per update, the bits of the plain sequential loop")
+
+        def med(xs):
+            return {"min": min(xs), "median": statistics.median(xs), "max": max(xs)}
+
+        hm = modes[0]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 f ~ U(-1,1))",
             "config": {"workload": workload(n, sweeps, args.precision), "n": n, "sweeps": sweeps,
-                       "kernel": ("all sweeps in one cooperative launch (grid barrier between colours)"
-                                  if persistent else {1: "one launch per colour", 2: "temporal (TMA tiles)",
-                                                      3: "register wavefront"}[kernel]),
-                       "update": ("fused: the five binary64 terms summed exactly in 64-bit fixed point, one "
-                                  "rounding to binary64 per update (<= 1e-13 relative max-norm of the "
-                                  "bit-exact iterate)" if args.fma else
-                                  "bit-exact: four correctly rounded FP64 adds per update, the bits of the "
-                                  "plain sequential loop"),
-                       "tblock_k": kdepth if blocked else None, "precision": args.precision,
+                       "kernel": head["kernel"], "update": update_desc(hm),
+                       "tblock_k": head["kdepth"] if head["blocked"] else None, "precision": args.precision,
                        "fp64_emulate": args.emulate, "tile_rows": args.tile_rows or "auto",
                        "sweep_values": args.values or "auto", "sweep_rows": args.rows or "auto",
                        "int_rows": args.int_rows,
                        "l2": "inputs larger than L2 (4 colour arrays of 1.08 GB each)",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs_algorithmic": BYTES_PER_LUP * lups / elapsed / 1e9,
-            "final_rho": rho,
-            "roofline": roofline,
+            "final_rho": head["rho"],
+            "roofline": head["roofline"],
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": clocks.summary(),
+            "gpu_launches": head["launches"],
+            "clocks": head["clocks"],
             "time_to_residual": ttr,
             "small_grid": small,
-            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
-            "sweeps_ms": {"min": min(sweep_ms), "median": statistics.median(sweep_ms), "max": max(sweep_ms),
-                          "note": "device time of the sweeps alone in each step"},
+            "step_ms": med(head["step_ms"]),
+            "sweeps_ms": dict(med(head["sweep_ms"]), note="device time of the sweeps alone in each step"),
         }
+        for fma in modes[1:]:  # the other update form, same workload, same run
+            r = results[fma]
+            line["bit_exact" if fma == 0 else "fused"] = {
+                "value": r["value"], "unit": UNIT, "ms_per_step": 1e3 * r["elapsed"] / args.steps,
+                "update": update_desc(fma), "kernel": r["kernel"], "roofline": r["roofline"],
+                "hbm_gbs_algorithmic": BYTES_PER_LUP * r["lups"] / r["elapsed"] / 1e9,
+                "final_rho": r["rho"], "gpu_launches": r["launches"], "clocks": r["clocks"],
+                "step_ms": med(r["step_ms"])}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -179,6 +179,26 @@ rbgs_status rbgs_set_solution(rbgs_t ctx, const double *u_in);
  */
 rbgs_status rbgs_set_problem(rbgs_t ctx, const double *f, const double *u_init);
 
+/*
+ * Not in the paper: library mechanics for serving a stream of problems of the context's
+ * size (same N and h2; each is Section 2's problem, swept by Eq. (1)).  For problem
+ * q = 0 .. count-1, in order: load f[q] and u_init[q] (as rbgs_set_problem), nsweeps
+ * sweeps (as rbgs_sweep, with the context's options), the residual rho[q] (as
+ * rbgs_residual; rho may be NULL) and the solution into u_out[q] (as rbgs_get_solution).
+ * Host buffers move on the library's own copy streams, one per direction, through
+ * double-buffered device staging: problem q+1's inputs and problem q-1's solution travel
+ * while problem q sweeps.  With page-locked host memory (cudaHostAlloc or registered) the
+ * copies run asynchronously; pageable memory works, but its copies hold the calling thread.
+ * Device buffers are used in place.  The staging (two natural-layout copies of f and u_init
+ * and two of u_out, for the directions that see host memory) is allocated on first use and
+ * kept with the context.  Returns once every solution is in place; work the caller queues
+ * on the context's stream afterwards follows all of it.  RBGS_ENONFINITE when some rho is
+ * not finite (every output is still written); the context then holds the last problem.
+ * RBGS_FP64 contexts only (fma 0 or 1).
+ */
+rbgs_status rbgs_run_stream(rbgs_t ctx, int count, const double *const *f, const double *const *u_init,
+                            long nsweeps, double *const *u_out, double *rho);
+
 /* Problem n of a batch: interior size, h^2, f (N*N) and u_init ((N+2)^2). */
 typedef struct {
     int n;

@@ -62,6 +62,10 @@ def _load():
         lib.ref_refine_solve.restype = c_long
         lib.ref_sweeps_fused.argtypes = [c_int, c_int, c_double, dp, dp, c_long, c_int, dp]
         lib.ref_sweeps_fused.restype = None
+        lib.ref_sweeps3d_f64.argtypes = [c_int, c_double, dp, dp, c_long]
+        lib.ref_sweeps3d_f64.restype = None
+        lib.ref_residual3d_f64.argtypes = [c_int, c_double, dp, dp, dp, dp]
+        lib.ref_residual3d_f64.restype = c_double
         _lib = lib
     return _lib
 
@@ -182,3 +186,30 @@ def window_value(f_full: np.ndarray, u0_full: np.ndarray, h2: float, nsweeps: in
     else:
         sweeps(u, f, h2, nsweeps, parity)
     return float(u[i - a + 1, j - c + 1])
+
+
+def _check3(u, f):
+    if u.dtype != np.float64 or f.dtype != np.float64:
+        raise TypeError("expected float64 arrays")
+    if not (u.flags.c_contiguous and f.flags.c_contiguous):
+        raise ValueError("arrays must be C-contiguous")
+    n = f.shape[0]
+    if f.shape != (n, n, n) or u.shape != (n + 2, n + 2, n + 2):
+        raise ValueError(f"f must be n^3 and u (n+2)^3, got {f.shape} and {u.shape}")
+    return n
+
+
+def sweeps3d(u: np.ndarray, f: np.ndarray, h2: float, nsweeps: int) -> np.ndarray:
+    """nsweeps red+black sweeps of the 7-point 3D update (the paper's 3D outlook, Section 5:
+    Eq. (1) with six neighbours, divided by 6), in place on u ((n+2)^3 with the shell)."""
+    n = _check3(u, f)
+    _load().ref_sweeps3d_f64(n, float(h2), _dptr(f), _dptr(u), int(nsweeps))
+    return u
+
+
+def residual3d(u: np.ndarray, f: np.ndarray, h2: float) -> tuple[float, float, float]:
+    """(rho, sum rt^2, sum hb^2) of the 3D system, the shell folded into b."""
+    n = _check3(u, f)
+    r2, b2 = ctypes.c_double(), ctypes.c_double()
+    rho = _load().ref_residual3d_f64(n, float(h2), _dptr(f), _dptr(u), ctypes.byref(r2), ctypes.byref(b2))
+    return rho, r2.value, b2.value

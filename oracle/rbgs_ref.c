@@ -320,3 +320,82 @@ void ref_sweeps_fused(int ni, int nj, double h2, const double *f, double *u, lon
         done += m;
     }
 }
+
+/*
+ * The three-dimensional variant (the paper's outlook, Section 5, names 3D problems as
+ * future work for the red-black scheme): -Lap u = f on the unit cube, u = g on its
+ * boundary, h = 1/(N+1), and the 7-point analogue of Eq. (1),
+ *
+ *     u_ijk <- (h^2 f_ijk + u_{i-1,j,k} + u_{i+1,j,k} + u_{i,j-1,k} + u_{i,j+1,k}
+ *                         + u_{i,j,k-1} + u_{i,j,k+1}) / 6,
+ *
+ * summed left to right in that order and divided by 6 (one correctly rounded division).
+ * A point is red when i + j + k is even; a sweep updates every red point, then every
+ * black one.  Storage: the natural (N+2)^3 grid u[i][j][k] (k fastest) with the boundary
+ * shell, and an N^3 array f.
+ */
+#define U3(i, j, k) u[((size_t)(i) * (size_t)(n + 2) + (size_t)(j)) * (size_t)(n + 2) + (size_t)(k)]
+#define F3(i, j, k) f[((size_t)((i) - 1) * (size_t)n + (size_t)((j) - 1)) * (size_t)n + (size_t)((k) - 1)]
+
+void ref_sweeps3d_f64(int n, double h2, const double *f, double *u, long nsweeps)
+{
+    for (long it = 0; it < nsweeps; ++it) {
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int i = 1; i <= n; ++i) {
+                for (int j = 1; j <= n; ++j) {
+                    for (int k = 1; k <= n; ++k) {
+                        if (((i + j + k) & 1) != colour)
+                            continue;
+                        double s = h2 * F3(i, j, k);
+                        s = s + U3(i - 1, j, k);
+                        s = s + U3(i + 1, j, k);
+                        s = s + U3(i, j - 1, k);
+                        s = s + U3(i, j + 1, k);
+                        s = s + U3(i, j, k - 1);
+                        s = s + U3(i, j, k + 1);
+                        U3(i, j, k) = s / 6.0;
+                    }
+                }
+            }
+        }
+    }
+}
+
+/*
+ * Scaled residual of the 3D system: rt = (h^2 f + the six neighbours, in the update's
+ * order) - 6 u at every interior point, hb = h^2 f plus the neighbours on the boundary
+ * shell (in the same order); rho = sqrt(sum rt^2) / sqrt(sum hb^2) (sqrt(sum rt^2) when
+ * b = 0), sums in plain i-major order.
+ */
+double ref_residual3d_f64(int n, double h2, const double *f, const double *u, double *sum_r2,
+                          double *sum_b2)
+{
+    double r2 = 0.0, b2 = 0.0;
+    for (int i = 1; i <= n; ++i) {
+        for (int j = 1; j <= n; ++j) {
+            for (int k = 1; k <= n; ++k) {
+                double hf = h2 * F3(i, j, k);
+                double s = hf;
+                s = s + U3(i - 1, j, k);
+                s = s + U3(i + 1, j, k);
+                s = s + U3(i, j - 1, k);
+                s = s + U3(i, j + 1, k);
+                s = s + U3(i, j, k - 1);
+                s = s + U3(i, j, k + 1);
+                double r = s - 6.0 * U3(i, j, k);
+                r2 = r2 + r * r;
+                double b = hf;
+                if (i == 1) b = b + U3(i - 1, j, k);
+                if (i == n) b = b + U3(i + 1, j, k);
+                if (j == 1) b = b + U3(i, j - 1, k);
+                if (j == n) b = b + U3(i, j + 1, k);
+                if (k == 1) b = b + U3(i, j, k - 1);
+                if (k == n) b = b + U3(i, j, k + 1);
+                b2 = b2 + b * b;
+            }
+        }
+    }
+    if (sum_r2) *sum_r2 = r2;
+    if (sum_b2) *sum_b2 = b2;
+    return b2 > 0.0 ? sqrt(r2) / sqrt(b2) : sqrt(r2);
+}

@@ -30,7 +30,7 @@ RBGS_KERNEL_AUTO, RBGS_KERNEL_COLOUR, RBGS_KERNEL_TEMPORAL, RBGS_KERNEL_WAVEFRON
 # Every symbol include/rbgs.h declares.
 EXPORTED = ("rbgs_default_opts", "rbgs_create", "rbgs_sweep", "rbgs_residual", "rbgs_solve",
             "rbgs_get_solution", "rbgs_set_solution", "rbgs_set_problem", "rbgs_solve_batched", "rbgs_destroy",
-            "rbgs_last_error", "rbgs_residual_static", "rbgs_batched_last_shape")
+            "rbgs_last_error", "rbgs_residual_static", "rbgs_batched_last_shape", "rbgs_run_stream")
 
 
 class RbgsError(RuntimeError):
@@ -100,6 +100,19 @@ def load_library(path: str | None = None):
     lib.rbgs_residual_static.restype = c_int
     lib.rbgs_last_error.argtypes = []
     lib.rbgs_last_error.restype = ctypes.c_char_p
+    lib.rbgs_run_stream.argtypes = [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), c_long, ctypes.POINTER(vp),
+                                    ctypes.POINTER(c_double)]
+    lib.rbgs_run_stream.restype = c_int
+    lib.rbgs3d_create.argtypes = [c_int, c_double, vp, vp, vp, ctypes.POINTER(vp)]
+    lib.rbgs3d_create.restype = c_int
+    lib.rbgs3d_sweep.argtypes = [vp, c_long]
+    lib.rbgs3d_sweep.restype = c_int
+    lib.rbgs3d_residual.argtypes = [vp, ctypes.POINTER(c_double)]
+    lib.rbgs3d_residual.restype = c_int
+    lib.rbgs3d_get_solution.argtypes = [vp, vp]
+    lib.rbgs3d_get_solution.restype = c_int
+    lib.rbgs3d_destroy.argtypes = [vp]
+    lib.rbgs3d_destroy.restype = None
     lib.rbgs_batched_last_shape.argtypes = [ctypes.POINTER(c_int)] * 5
     lib.rbgs_batched_last_shape.restype = None
     _lib = lib
@@ -190,6 +203,21 @@ def rbgs_set_problem(ctx: int, f, u_init) -> None:
     _check(load_library().rbgs_set_problem(ctx, _ptr(f), _ptr(u_init)))
 
 
+def rbgs_run_stream(ctx: int, f_list, u_init_list, nsweeps: int, u_out_list,
+                    allow_nonfinite: bool = False) -> list[float]:
+    """rbgs_run_stream: a stream of problems of the context's size through one context,
+    the host copies overlapping the neighbouring problems' sweeps; returns the rho values."""
+    k = len(f_list)
+    if not (len(u_init_list) == len(u_out_list) == k):
+        raise ValueError("f, u_init and u_out lists must have the same length")
+    arr = lambda xs: (ctypes.c_void_p * max(k, 1))(*[_ptr(x) for x in xs])
+    rho = (ctypes.c_double * max(k, 1))()
+    allowed = (RBGS_OK, RBGS_ENONFINITE) if allow_nonfinite else (RBGS_OK,)
+    _check(load_library().rbgs_run_stream(ctx, k, arr(f_list), arr(u_init_list), int(nsweeps), arr(u_out_list),
+                                          rho), allowed)
+    return list(rho[:k])
+
+
 def rbgs_destroy(ctx: int) -> None:
     if ctx:
         load_library().rbgs_destroy(ctx)
@@ -268,9 +296,52 @@ class Solver:
     def set_problem(self, f, u_init) -> None:
         rbgs_set_problem(self.ctx, f, u_init)
 
+    def run_stream(self, f_list, u_init_list, nsweeps: int, u_out_list, allow_nonfinite: bool = False):
+        return rbgs_run_stream(self.ctx, f_list, u_init_list, nsweeps, u_out_list, allow_nonfinite)
+
     def close(self) -> None:
         if self.ctx:
             rbgs_destroy(self.ctx)
+            self.ctx = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver3D:
+    """The 3D variant (include/rbgs3d.h): ``with Solver3D(n, h2, f, u0) as s: s.sweep(10)``.
+    f is n^3, u (n+2)^3 with the boundary shell, float64, host or device."""
+
+    def __init__(self, n, h2, f, u_init, stream=None):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        s = _stream_of(f, u_init, stream=stream)
+        _check(lib.rbgs3d_create(int(n), float(h2), _ptr(f), _ptr(u_init), s, ctypes.byref(h)))
+        self.n, self.ctx = n, h.value
+
+    def sweep(self, nsweeps: int) -> None:
+        _check(load_library().rbgs3d_sweep(self.ctx, int(nsweeps)))
+
+    def residual(self) -> float:
+        rel = ctypes.c_double()
+        _check(load_library().rbgs3d_residual(self.ctx, ctypes.byref(rel)))
+        return rel.value
+
+    def get_solution(self, u_out) -> None:
+        _check(load_library().rbgs3d_get_solution(self.ctx, _ptr(u_out)))
+
+    def close(self) -> None:
+        if self.ctx:
+            load_library().rbgs3d_destroy(self.ctx)
             self.ctx = 0
 
     def __enter__(self):

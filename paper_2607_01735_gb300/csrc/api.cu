@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "sweep_impl.cuh"
@@ -127,6 +128,19 @@ void free_ctx(rbgs_ctx *c) {
     cudaFree(c->hq[0]);
     cudaFree(c->hq[1]);
     cudaFree(c->fwords);
+    for (int q = 0; q < 2; ++q) {
+        cudaFree(c->sin_f[q]);
+        cudaFree(c->sin_u[q]);
+        cudaFree(c->sout[q]);
+        if (c->ev_copied[q]) cudaEventDestroy(c->ev_copied[q]);
+        if (c->ev_packed[q]) cudaEventDestroy(c->ev_packed[q]);
+        if (c->ev_unpacked[q]) cudaEventDestroy(c->ev_unpacked[q]);
+        if (c->ev_out[q]) cudaEventDestroy(c->ev_out[q]);
+    }
+    if (c->h2d) cudaStreamDestroy(c->h2d);
+    if (c->d2h) cudaStreamDestroy(c->d2h);
+    cudaFree(c->dres);
+    if (c->hres) cudaFreeHost(c->hres);
     cudaFree(c->staging);
     cudaFree(c->partials);
     cudaFree(c->dsum);
@@ -366,6 +380,43 @@ rbgs_status refine_solve(rbgs_ctx *c, double tol, long *done_out, double *rho_ou
         st = RBGS_ENOTCONV;
     }
     return st;
+}
+
+// Buffers, copy streams and events of rbgs_run_stream (allocated on first use; staging
+// only for the directions that see host memory).
+rbgs_status ensure_stream(rbgs_ctx *c, bool in_host, bool out_host, int count) {
+    const size_t nat_f = (size_t)c->g.n * c->g.n * sizeof(double);
+    const size_t nat_u = (size_t)c->g.rows * c->g.rows * sizeof(double);
+    bool ok = true;
+    for (int q = 0; q < 2 && ok; ++q) {
+        if (in_host && !c->sin_f[q])
+            ok = cudaMalloc(&c->sin_f[q], nat_f) == cudaSuccess && cudaMalloc(&c->sin_u[q], nat_u) == cudaSuccess;
+        if (ok && out_host && !c->sout[q]) ok = cudaMalloc(&c->sout[q], nat_u) == cudaSuccess;
+        if (ok && !c->ev_copied[q])
+            ok = cudaEventCreateWithFlags(&c->ev_copied[q], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->ev_packed[q], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->ev_unpacked[q], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->ev_out[q], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (ok && !c->h2d)
+        ok = cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok && (size_t)count > c->res_cap) {
+        cudaFree(c->dres);
+        if (c->hres) cudaFreeHost(c->hres);
+        c->dres = nullptr;
+        c->hres = nullptr;
+        c->res_cap = 0;
+        ok = cudaMalloc(&c->dres, 2 * (size_t)count * sizeof(double)) == cudaSuccess &&
+             cudaMallocHost(&c->hres, 2 * (size_t)count * sizeof(double)) == cudaSuccess;
+        if (ok) c->res_cap = (size_t)count;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        set_error("rbgs_run_stream: allocation of staging buffers, streams or events failed");
+        return RBGS_ENOMEM;
+    }
+    return RBGS_OK;
 }
 
 }  // namespace
@@ -653,6 +704,107 @@ rbgs_status rbgs_set_problem(rbgs_t c, const double *f, const double *u_init) {
     clear_error();
     if (!c || !f || !u_init) { set_error("ctx, f and u_init must not be NULL"); return RBGS_EINVAL; }
     return load_problem(c, f, u_init);
+}
+
+rbgs_status rbgs_run_stream(rbgs_t c, int count, const double *const *f, const double *const *u_init, long nsweeps,
+                            double *const *u_out, double *rho) {
+    clear_error();
+    if (!c || count < 0 || nsweeps < 0 || (count > 0 && (!f || !u_init || !u_out))) {
+        set_error("rbgs_run_stream: ctx, f, u_init and u_out must be given, count and nsweeps >= 0");
+        return RBGS_EINVAL;
+    }
+    for (int q = 0; q < count; ++q) {
+        if (!f[q] || !u_init[q] || !u_out[q]) {
+            set_error("rbgs_run_stream: problem %d has a NULL pointer", q);
+            return RBGS_EINVAL;
+        }
+    }
+    if (count == 0) return RBGS_OK;
+    if (c->opts.precision != RBGS_FP64) {
+        set_error("rbgs_run_stream runs RBGS_FP64 sweeps (fused or bit-exact)");
+        return RBGS_EINVAL;
+    }
+    const Geometry &g = c->g;
+    const size_t bytes_f = (size_t)g.n * g.n * sizeof(double), bytes_u = (size_t)g.rows * g.rows * sizeof(double);
+    std::vector<char> in_dev(count), out_dev(count);
+    bool any_in_host = false, any_out_host = false;
+    for (int q = 0; q < count; ++q) {
+        in_dev[q] = device_accessible(f[q]) && device_accessible(u_init[q]);
+        out_dev[q] = device_accessible(u_out[q]);
+        any_in_host |= !in_dev[q];
+        any_out_host |= !out_dev[q];
+    }
+    rbgs_status st = ensure_stream(c, any_in_host, any_out_host, count);
+    if (st != RBGS_OK) return st;
+    cudaStream_t ms = c->stream;
+    // host -> device copy of problem q's inputs into staging buffer q % 2, once the pack of
+    // problem q - 2 (the buffer's previous reader) has run
+    auto copy_in = [&](int q) -> rbgs_status {
+        if (in_dev[q]) return RBGS_OK;
+        const int b = q & 1;
+        if (q >= 2) RBGS_CUDA(cudaStreamWaitEvent(c->h2d, c->ev_packed[b], 0));
+        RBGS_CUDA(cudaMemcpyAsync(c->sin_f[b], f[q], bytes_f, cudaMemcpyDefault, c->h2d));
+        RBGS_CUDA(cudaMemcpyAsync(c->sin_u[b], u_init[q], bytes_u, cudaMemcpyDefault, c->h2d));
+        RBGS_CUDA(cudaEventRecord(c->ev_copied[b], c->h2d));
+        return RBGS_OK;
+    };
+    // the caller's earlier work on the context's stream comes first
+    RBGS_CUDA(cudaEventRecord(c->ev_unpacked[1], ms));
+    RBGS_CUDA(cudaStreamWaitEvent(c->h2d, c->ev_unpacked[1], 0));
+    RBGS_CUDA(cudaStreamWaitEvent(c->d2h, c->ev_unpacked[1], 0));
+    if ((st = copy_in(0)) != RBGS_OK) return st;
+    for (int q = 0; q < count; ++q) {
+        const int b = q & 1;
+        const double *fv = f[q], *uv = u_init[q];
+        if (!in_dev[q]) {
+            RBGS_CUDA(cudaStreamWaitEvent(ms, c->ev_copied[b], 0));
+            fv = c->sin_f[b];
+            uv = c->sin_u[b];
+        }
+        if ((st = enqueue_pack(c, fv, uv)) != RBGS_OK) return st;
+        RBGS_CUDA(cudaEventRecord(c->ev_packed[b], ms));
+        RBGS_CUDA(cudaMemcpyAsync(c->dres + 2 * q, c->dsum + 1, sizeof(double), cudaMemcpyDeviceToDevice, ms));
+        // the next problem's inputs move while this one sweeps
+        if (q + 1 < count && (st = copy_in(q + 1)) != RBGS_OK) return st;
+        if (nsweeps > 0) {
+            if ((st = sweeps_f64(c, nsweeps)) != RBGS_OK) return st;
+            c->black_fresh = !c->fused;
+        }
+        if ((st = launch_residual_sum(c, ms)) != RBGS_OK) return st;
+        RBGS_CUDA(cudaMemcpyAsync(c->dres + 2 * q + 1, c->dsum, sizeof(double), cudaMemcpyDeviceToDevice, ms));
+        if (out_dev[q]) {
+            if ((st = launch_unpack_u(g, c->f64.u[0], c->f64.u[1], u_out[q], ms)) != RBGS_OK) return st;
+        } else {
+            // staging buffer b is free once the copy-out of problem q - 2 has finished; this
+            // solution then leaves while the next problem sweeps
+            if (q >= 2) RBGS_CUDA(cudaStreamWaitEvent(ms, c->ev_out[b], 0));
+            if ((st = launch_unpack_u(g, c->f64.u[0], c->f64.u[1], c->sout[b], ms)) != RBGS_OK) return st;
+            RBGS_CUDA(cudaEventRecord(c->ev_unpacked[b], ms));
+            RBGS_CUDA(cudaStreamWaitEvent(c->d2h, c->ev_unpacked[b], 0));
+            RBGS_CUDA(cudaMemcpyAsync(u_out[q], c->sout[b], bytes_u, cudaMemcpyDefault, c->d2h));
+            RBGS_CUDA(cudaEventRecord(c->ev_out[b], c->d2h));
+        }
+    }
+    RBGS_CUDA(cudaMemcpyAsync(c->hres, c->dres, 2 * (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, ms));
+    // later work on the context's stream (and events the caller records there) follows the
+    // last copies
+    RBGS_CUDA(cudaEventRecord(c->ev_copied[0], c->h2d));
+    RBGS_CUDA(cudaEventRecord(c->ev_out[0], c->d2h));
+    RBGS_CUDA(cudaStreamWaitEvent(ms, c->ev_copied[0], 0));
+    RBGS_CUDA(cudaStreamWaitEvent(ms, c->ev_out[0], 0));
+    if ((st = check_device_status(c)) != RBGS_OK) return st;
+    rbgs_status result = RBGS_OK;
+    for (int q = 0; q < count; ++q) {
+        const double den2 = c->hres[2 * q], r2 = c->hres[2 * q + 1];
+        const double r = den2 > 0.0 ? std::sqrt(r2) / std::sqrt(den2) : std::sqrt(r2);
+        if (rho) rho[q] = r;
+        if (!std::isfinite(r) && result == RBGS_OK) {
+            set_error("rbgs_run_stream: problem %d: residual is not finite", q);
+            result = RBGS_ENONFINITE;
+        }
+    }
+    c->den2 = c->hres[2 * (count - 1)];
+    return result;
 }
 
 void rbgs_destroy(rbgs_t c) {

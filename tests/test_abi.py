@@ -25,7 +25,7 @@ def lib():
 def _declared(path=HEADER):
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(rbgs_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(rbgs[a-z0-9]*_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_binding_names():
@@ -35,7 +35,7 @@ def test_header_declares_the_binding_names():
 def test_library_exports_every_declared_symbol(lib):
     import subprocess
     out = subprocess.run(["nm", "-D", "--defined-only", rb.LIB_PATH], capture_output=True, text=True).stdout
-    exported = set(re.findall(r" T (rbgs_\w+)", out))
+    exported = set(re.findall(r" T (rbgs\w*)", out))
     assert len(HEADERS) >= 2
     for h in HEADERS:
         names = _declared(h)
@@ -53,7 +53,7 @@ def _declaration_comments(path):
     precedes the declaration, or, for declarations grouped under one comment, that one."""
     text = open(path).read()
     out, last_comment = [], ""
-    for m in re.finditer(r"/\*.*?\*/|\b(rbgs_[a-z0-9_]+)\s*\(", text, flags=re.S):
+    for m in re.finditer(r"/\*.*?\*/|\b(rbgs[a-z0-9]*_[a-z0-9_]+)\s*\(", text, flags=re.S):
         if m.group(0).startswith("/*"):
             last_comment = m.group(0)
         else:
@@ -123,6 +123,19 @@ def test_argument_errors_without_gpu(lib):
                 rb.default_opts(max_seconds=float("nan")), rb.default_opts(max_seconds=float("inf"))):
         assert lib.rbgs_create(4, 0.04, f.ctypes.data, u.ctypes.data, ctypes.byref(bad), None,
                                ctypes.byref(h)) == rb.RBGS_EINVAL
+    vpa = ctypes.c_void_p * 1
+    assert lib.rbgs_run_stream(None, 1, vpa(f.ctypes.data), vpa(u.ctypes.data), 1, vpa(u.ctypes.data),
+                               None) == rb.RBGS_EINVAL
+    # the 3D variant checks its arguments on the host too
+    f3, u3 = np.zeros((2, 2, 2)), np.zeros((4, 4, 4))
+    assert lib.rbgs3d_create(0, 0.1, f3.ctypes.data, u3.ctypes.data, None, ctypes.byref(h)) == rb.RBGS_EINVAL
+    assert lib.rbgs3d_create(4096, 0.1, f3.ctypes.data, u3.ctypes.data, None, ctypes.byref(h)) == rb.RBGS_EINVAL
+    assert lib.rbgs3d_create(2, -0.1, f3.ctypes.data, u3.ctypes.data, None, ctypes.byref(h)) == rb.RBGS_EINVAL
+    assert lib.rbgs3d_create(2, 0.1, None, u3.ctypes.data, None, ctypes.byref(h)) == rb.RBGS_EINVAL
+    assert lib.rbgs3d_sweep(None, 1) == rb.RBGS_EINVAL
+    assert lib.rbgs3d_residual(None, None) == rb.RBGS_EINVAL
+    assert lib.rbgs3d_get_solution(None, None) == rb.RBGS_EINVAL
+    lib.rbgs3d_destroy(None)
     assert lib.rbgs_sweep(None, 1) == rb.RBGS_EINVAL
     assert lib.rbgs_residual(None, None) == rb.RBGS_EINVAL
     assert lib.rbgs_solve(None, 1e-8, None, None) == rb.RBGS_EINVAL
