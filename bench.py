@@ -84,8 +84,12 @@ def parse():
     p.add_argument("--train-samples", type=int, default=4096, help="learned: training problems (255^2)")
     p.add_argument("--train-steps", type=int, default=3000, help="learned: Adam steps")
     p.add_argument("--eval-sizes", default="1023,4095", help="learned: held-out grid sizes")
-    p.add_argument("--eval-fields", type=int, default=2, help="learned: held-out fields per size")
-    p.add_argument("--eval-cap", default="2500000,400000", help="learned: sweep cap per solve, per size")
+    p.add_argument("--eval-fields", type=int, default=8, help="learned: held-out fields per size")
+    p.add_argument("--eval-cap", default="5000000,20000000", help="learned: sweep cap per solve, per size")
+    p.add_argument("--eval-starts", default="zero,coarse,full;zero,full",
+                   help="learned: guesses solved from, per size (';'-separated)")
+    p.add_argument("--plain-fields", default="8,1",
+                   help="learned: fields per size also solved from u0 = 0 by plain FP64 (fused update)")
     p.add_argument("--conv-batch", type=int, default=16, help="conv: batch of the layer inputs")
     p.add_argument("--conv-hw", type=int, default=256, help="conv: level-0 height = width")
     p.add_argument("--conv-layer", type=int, default=-1, help="conv: one layer index (-1: all 15)")
@@ -96,11 +100,14 @@ def parse():
     p.add_argument("--mixed-cap", type=int, default=20000, help="mixed: sweeps actually run per form")
     p.add_argument("--mixed-chunk", type=int, default=2000, help="mixed: sweeps between residual samples")
     p.add_argument("--mixed-tol", type=float, default=1e-10, help="mixed: relative residual target")
-    p.add_argument("--mode", choices=["grid", "batched", "learned", "conv", "mixed"], default="grid",
+    p.add_argument("--n3", type=int, default=511, help="3d: interior size per side")
+    p.add_argument("--mode", choices=["grid", "batched", "learned", "conv", "mixed", "3d"], default="grid",
                    help="grid: one large grid (default); batched: many uneven problems in one launch")
     p.add_argument("--nprob", type=int, default=512)
     p.add_argument("--sizes", default="63,127,255,511,1023", help="batched: allowed interior sizes")
     p.add_argument("--tol", type=float, default=1e-8, help="batched: relative residual target")
+    p.add_argument("--sequential", action="store_true",
+                   help="batched: also estimate the one-problem-at-a-time plain FP64 wall time")
     p.add_argument("--team", type=int, default=0,
                    help="batched: 0 autotuned, 1 one block per problem, 2/4 phased plan with clusters")
     p.add_argument("--no-e2e", action="store_true")
@@ -408,7 +415,12 @@ def run_batched(args):
     opts = rb.default_opts(precision=rb.RBGS_FP32_REFINE if refine else rb.RBGS_FP64,
                            inner_sweeps=args.inner, check_every=100, team_size=args.team)
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):  # warm-up (includes the launch-shape autotuning)
+    # the launch-shape autotuner runs on the first call for a size mix and caches its choice;
+    # a call capped at one sweep triggers it without a full solve
+    warm = rb.default_opts(precision=opts.precision, inner_sweeps=args.inner, check_every=100,
+                           team_size=args.team, max_sweeps=1)
+    rb.rbgs_solve_batched(probs, args.tol, outs, warm, allow_failures=True)
+    for _ in range(args.warmup):  # full warm-up solves
         rb.rbgs_solve_batched(probs, args.tol, outs, opts, allow_failures=True)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -443,6 +455,9 @@ def run_batched(args):
                 "glups": lups / t / 1e9, "total_sweeps": int(sum(r["sweeps"] for r in allres.values())),
                 "launch_shape": rb.rbgs_batched_last_shape(),
                 "step_s": [round(x, 4) for x in times]}
+        if args.sequential and world == 1:
+            line["sequential_plain_fp64"] = sequential_estimate(rb, torch, table, allres, args.tol, dev, stream)
+            line["sequential_plain_fp64"]["batched_speedup"] = line["sequential_plain_fp64"]["seconds"] / t
         alu, alu_src, hbm, hbm_src = device_peaks(dev)
         if refine:  # FP32 sweeps dominate; the problems are L2-resident, so this is a floor
             achieved = 12.0 * lups / t / 1e9
@@ -461,6 +476,93 @@ def run_batched(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def sequential_estimate(rb, torch, table, res, tol, dev, stream, probe_sweeps=2000):
+    """Wall time of solving the batch's problems one after another with plain FP64 rbgs_solve
+    (bit-exact, check every 100 sweeps, each problem on the whole GPU).  The batched FP64
+    iterate equals the single-problem solve bit for bit, so each problem's sweep count is the
+    batch's; per size, the cost of a sweep (check included) and of loading a problem are
+    measured on one context, and the time is the sum of count x cost.  An estimate from
+    measured costs, labelled as such (it avoids re-running the whole batch serially)."""
+    import synth
+    per_size = {}
+    for n in sorted({table[p]["n"] for p in res}):
+        p0 = next(p for p in res if table[p]["n"] == n)
+        f, u, h2 = synth.batched_problem(table[p0])
+        fd, ud = torch.from_numpy(f).to(dev), torch.from_numpy(u).to(dev)
+        with rb.Solver(n, h2, fd, ud, check_every=100, max_sweeps=probe_sweeps, stall_checks=-1) as s:
+            s.solve(0.0, allow_not_converged=True)  # warm: graphs, caches
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            s.set_problem(fd, ud)
+            e[1].record(stream)
+            s.solve(0.0, allow_not_converged=True)
+            e[2].record(stream)
+            torch.cuda.synchronize(dev)
+            per_size[n] = {"load_s": e[0].elapsed_time(e[1]) / 1e3,
+                           "s_per_sweep": e[1].elapsed_time(e[2]) / 1e3 / probe_sweeps}
+    total = sum(per_size[table[p]["n"]]["load_s"] + res[p]["sweeps"] * per_size[table[p]["n"]]["s_per_sweep"]
+                for p in res)
+    return {"seconds": total, "problems_per_s": len(res) / total, "per_size": per_size,
+            "how": f"estimate: per problem, its sweep count x the measured cost per sweep of rbgs_solve at its "
+                   f"size (check every 100, measured over {probe_sweeps} sweeps) + the measured load time"}
+
+
+def run_3d(args):
+    """The 3D variant (the paper's 3D outlook): n^3 interior, zero boundary shell,
+    f ~ U(-1,1) from stream 1, u0 = 0, `sweeps` 7-point red-black sweeps + the residual per
+    step, on one context (the problem reloaded each step from device memory)."""
+    import torch
+
+    import paper_2607_01735_gb300 as rb
+    import synth
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, sweeps = args.n3, args.sweeps
+    h2 = 1.0 / float(n + 1) ** 2
+    f = synth.uniform_pm1_grid(n * n, 1, device=dev, nj=n).reshape(n, n, n).contiguous()
+    u0 = torch.zeros(n + 2, n + 2, n + 2, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    with rb.Solver3D(n, h2, f, u0) as s:
+        for _ in range(args.warmup):
+            s.sweep(sweeps)
+        torch.cuda.synchronize(dev)
+        with ClockSampler(str(uuid) if uuid else None) as clocks:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                s.sweep(sweeps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        rho = s.residual()
+    secs = e0.elapsed_time(e1) / 1e3
+    lups = float(n) ** 3 * sweeps * args.steps
+    alu, alu_src, hbm, hbm_src = device_peaks(dev)
+    per_half = secs / (2 * sweeps * args.steps)
+    alg = 24.0 * n ** 3 / 2
+    line = {"metric": "GLUP/s (3D 7-point red-black sweeps)", "value": lups / secs / 1e9, "unit": "GLUP/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 f ~ U(-1,1))",
+            "config": {"workload": f"3D RBGS, {n}^3 interior, zero shell, f~U(-1,1) seed 1, u0=0, {sweeps} sweeps",
+                       "update": "six correctly rounded adds + one correctly rounded division by 6 (bit-exact)"},
+            "final_rho": rho,
+            "roofline": {"bound": "alu", "kernel": "half_sweep3_kernel", "launch_ms": 1e3 * per_half,
+                         "hbm": {"achieved": alg / per_half / 1e9, "peak": hbm, "unit": "GB/s",
+                                 "frac": alg / per_half / 1e9 / hbm, "peak_source": hbm_src},
+                         "achieved": 6.0 * n ** 3 / 2 / per_half / 1e12, "peak": alu, "unit": "TFLOP/s",
+                         "frac": 6.0 * n ** 3 / 2 / per_half / 1e12 / alu, "peak_source": alu_src,
+                         "note": "achieved counts the six adds per update only; the division by 6 runs on "
+                                 "the FP64 pipe too, so the pipe's true load is higher"},
+            "clocks": clocks.summary(), "gpu_launches": 2 * sweeps * args.steps}
+    print(json.dumps(line))
     return 0
 
 
@@ -498,6 +600,7 @@ def run_mixed(args):
     uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
     with ClockSampler(str(uuid) if uuid else None) as clocks:
         for name, kw in (("plain_fp64", dict(check_every=100)),
+                         ("plain_fp64_fused", dict(check_every=100, fma=1)),
                          ("fp32_refine", dict(precision=rb.RBGS_FP32_REFINE, inner_sweeps=100))):
             with rb.Solver(n, h2, f, u, max_sweeps=chunk, **kw) as sol:
                 rho0 = sol.residual()
@@ -533,7 +636,9 @@ def run_mixed(args):
                                    f"FP32 sweeps + FP64 refinement (100 inner) vs plain FP64",
                        "extrapolation": "measured cost per sweep x sweeps needed at the asymptotic "
                                         "rate cos^2(pi h) after the measured sweeps"},
-            "speedup_vs_plain_fp64": p_est / r_est, "forms": forms, "clocks": clocks.summary()}
+            "speedup_vs_plain_fp64": p_est / r_est,
+            "speedup_vs_plain_fp64_fused": forms["plain_fp64_fused"]["extrapolated"]["asymptotic_rate"]["seconds"] / r_est,
+            "forms": forms, "clocks": clocks.summary()}
     alu, alu_src, hbm, hbm_src = device_peaks(dev)
     r_bytes = 3.0 * 1e9 * forms["fp32_refine"]["glups"] / 1e9  # 12 B per point per 4-sweep pass
     line["roofline"] = {"bound": "hbm", "achieved": r_bytes, "peak": hbm, "unit": "GB/s", "frac": r_bytes / hbm,
@@ -737,6 +842,8 @@ def run_learned(args):
     torch.save(net.get_params().cpu(), os.path.join(OUT_DIR, "unet_params.pt"))
     results = []
     caps = [int(v) for v in args.eval_cap.split(",")]
+    starts = [v.split(",") for v in args.eval_starts.split(";")]
+    plain = [int(v) for v in args.plain_fields.split(",")]
     for si, n in enumerate(int(v) for v in args.eval_sizes.split(",")):
         cap = caps[min(si, len(caps) - 1)]
         h2 = synth.h_squared(n)
@@ -745,7 +852,15 @@ def run_learned(args):
             f, u = synth.learned_guess_sample(n, stream)
             fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u).cuda()
             row = {"n": n, "stream": stream}
-            for name in ("zero", "coarse", "full"):
+            if k < plain[min(si, len(plain) - 1)]:
+                # u0 = 0, plain FP64 sweeps (the fused update), to the same tolerance
+                t1 = time.perf_counter()
+                with rb.Solver(n, h2, fd, ud, fma=1, check_every=200, max_sweeps=cap) as s:
+                    sw, rho, _ = s.solve(args.tol, allow_not_converged=True)
+                torch.cuda.synchronize()
+                row["zero_plain_fp64_fused"] = {"sweeps": sw, "rho": rho, "solve_s": time.perf_counter() - t1,
+                                                "guess_s": 0.0, "sweeps_to_tol_extrapolated": None}
+            for name in starts[min(si, len(starts) - 1)]:
                 t1 = time.perf_counter()
                 if name == "zero":
                     u0 = ud
@@ -784,6 +899,8 @@ def main():
         return run_conv(args)
     if args.mode == "mixed":
         return run_mixed(args)
+    if args.mode == "3d":
+        return run_3d(args)
     import torch
     import torch.distributed as dist
 

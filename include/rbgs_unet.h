@@ -129,6 +129,47 @@ rbgs_status rbgs_unet_train_step(rbgs_unet_t net, const float *x, const float *t
  * ignored). */
 void rbgs_unet_destroy(rbgs_unet_t net);
 
+/* ------------------------------------------------------- grids of the guess --- */
+
+/*
+ * Not in the paper (learned initial guess).  Grid operations around the network, all on
+ * device memory of the current device, asynchronous on the stream; g = n + 2 and
+ * (n+2)^2 grids are row-major with the Dirichlet ring.  The transfinite (Coons)
+ * interpolation of a ring, at point (i, j) with x = i/(g-1), y = j/(g-1), is
+ *   (1-x) N_j + x S_j + (1-y) W_i + y E_i - ((1-x)(1-y) c00 + (1-x) y c01 + x (1-y) c10 + x y c11)
+ * (N, S, W, E: rows 0, g-1 and columns 0, g-1; c: the corners).  It reproduces ring data
+ * linear in x and in y, and the ring itself.
+ *   rbgs_guess_blend:    out (g^2 doubles) = that interpolation of u_ring's ring.
+ *   rbgs_guess_input:    x (size^2 x 4 floats, channels fastest; size >= g, a multiple of 8)
+ *                        = f on the interior, the ring mask, the ring values, the blend;
+ *                        zero outside the g x g corner.
+ *   rbgs_guess_target:   t (size^2 floats) = sol - blend on the g x g corner, zero elsewhere
+ *                        (what the network learns: the correction to the blend).
+ *   rbgs_guess_assemble: u0 (g^2 doubles) = the ring of u_ring, interior blend + pred
+ *                        (pred: size^2 floats, the network's output).
+ * EINVAL for n < 1, a bad size or a pointer that is not device memory.
+ */
+rbgs_status rbgs_guess_blend(const double *u_ring, int n, double *out, void *cuda_stream);
+rbgs_status rbgs_guess_input(const double *f, const double *u_ring, int n, int size, float *x, void *cuda_stream);
+rbgs_status rbgs_guess_target(const double *sol, const double *u_ring, int n, int size, float *t,
+                              void *cuda_stream);
+rbgs_status rbgs_guess_assemble(const double *u_ring, const float *pred, int n, int size, double *u0,
+                                void *cuda_stream);
+
+/*
+ * Not in the paper (learned initial guess).  Transfer between a fine n^2 grid and a coarse
+ * nc^2 training grid whose nodes are fine nodes: r = (n+1)/(nc+1) must be an integer
+ * (EINVAL otherwise), coarse node (ci, cj) sits on fine node (ci r, cj r).
+ *   rbgs_guess_coarsen: fc (nc^2) = the mean of f over the (2r-1)^2 fine interior nodes
+ *                       around each coarse interior node; uc_ring ((nc+2)^2) = u_ring at
+ *                       the coarse nodes.
+ *   rbgs_guess_refine:  u0 ((n+2)^2) = the bilinear interpolation of uc ((nc+2)^2) at the
+ *                       fine interior nodes, the ring of u_ring.
+ */
+rbgs_status rbgs_guess_coarsen(const double *f, const double *u_ring, int n, int nc, double *fc, double *uc_ring,
+                               void *cuda_stream);
+rbgs_status rbgs_guess_refine(const double *uc, int nc, const double *u_ring, int n, double *u0, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

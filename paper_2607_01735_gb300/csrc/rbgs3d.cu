@@ -14,13 +14,15 @@
 // adjacent in the item order and lines i+-1 one plane apart, so the re-reads of the other
 // colour hit the caches (a plane of a 511^3 grid is 1.2 MB).  Arithmetic: six adds in the
 // order above, each one correctly rounded fused multiply-add by a run-time 1.0, and one
-// correctly rounded division: the same bits as the plain sequential loop.
+// correctly rounded division by 6 (div6 in div6.cuh: three FP64 operations instead of the
+// division sequence): the same bits as the plain sequential loop.
 #include <algorithm>
 #include <cmath>
 #include <new>
 
 #include "../../include/rbgs3d.h"
 #include "common.cuh"
+#include "div6.cuh"
 #include "fp64.cuh"
 #include "sweep_impl.cuh"
 
@@ -88,8 +90,6 @@ __global__ void unpack3_kernel(const double *__restrict__ u0, const double *__re
         if (k + 1 <= n + 1) u_nat[line * L + k + 1] = (even ? u1 : u0)[q];
     }
 }
-
-__device__ __forceinline__ double div6(double s) { return __ddiv_rn(s, 6.0); }
 
 // One half-sweep of colour C: items (interior line, pair of values) over the grid.
 template <int C>

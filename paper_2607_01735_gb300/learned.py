@@ -18,10 +18,9 @@ from __future__ import annotations
 
 import numpy as np
 import torch
-import torch.nn.functional as F
 
 from . import default_opts, rbgs_solve_batched, RBGS_FP64, RBGS_FP32_REFINE
-from .unet import UNet, boundary_blend, network_input
+from .unet import UNet, guess_assemble, guess_coarsen, guess_refine, guess_target, network_input
 
 
 def grid_size(n: int) -> int:
@@ -52,9 +51,7 @@ def make_dataset(n: int, streams, tol: float = 1e-12, device="cuda", batch: int 
         for (nn, _, fd, ud), sol in zip(probs, outs):
             xs.append(network_input(fd, ud, size))
             # the network learns the correction to the boundary interpolation
-            t = torch.zeros((size, size), dtype=torch.float32, device=device)
-            t[:n + 2, :n + 2] = (sol - boundary_blend(ud)).to(torch.float32)
-            ys.append(t)
+            ys.append(guess_target(sol, ud, size))
     x = torch.stack(xs)
     y = torch.stack(ys)
     mask = torch.zeros((size, size), dtype=torch.float32, device=device)
@@ -81,13 +78,8 @@ def initial_guess(net: UNet, f: torch.Tensor, u_ring: torch.Tensor) -> torch.Ten
     """u0 on the (n+2)^2 grid: boundary interpolation plus the network's correction in the
     interior, the given Dirichlet ring."""
     n = f.shape[0]
-    size = grid_size(n)
-    x = network_input(f, u_ring, size).unsqueeze(0)
-    pred = net.forward(x)[0]
-    u0 = u_ring.clone().to(torch.float64)
-    base = boundary_blend(u_ring)
-    u0[1:n + 1, 1:n + 1] = base[1:n + 1, 1:n + 1] + pred[1:n + 1, 1:n + 1].to(torch.float64)
-    return u0
+    x = network_input(f, u_ring, grid_size(n)).unsqueeze(0)
+    return guess_assemble(u_ring, net.forward(x)[0])
 
 
 def initial_guess_coarse(net: UNet, f: torch.Tensor, u_ring: torch.Tensor, n_coarse: int) -> torch.Tensor:
@@ -95,20 +87,7 @@ def initial_guess_coarse(net: UNet, f: torch.Tensor, u_ring: torch.Tensor, n_coa
     the fine grid; the fine Dirichlet ring is kept.  (n + 1) must be a multiple of
     (n_coarse + 1) so that coarse nodes coincide with fine nodes."""
     n = f.shape[0]
-    r = (n + 1) // (n_coarse + 1)
-    if r * (n_coarse + 1) != n + 1:
+    if (n + 1) % (n_coarse + 1):
         raise ValueError("(n + 1) must be a multiple of (n_coarse + 1)")
-    # f at coarse interior nodes: average of the fine nodes around each coarse node
-    fpad = torch.zeros((n + 2, n + 2), dtype=torch.float64, device=f.device)
-    fpad[1:n + 1, 1:n + 1] = f
-    k = 2 * r - 1
-    avg = F.avg_pool2d(fpad[None, None], kernel_size=k, stride=1, padding=r - 1)[0, 0]
-    idx = torch.arange(1, n_coarse + 1, device=f.device) * r
-    fc = avg[idx][:, idx]
-    ring_idx = torch.arange(0, n_coarse + 2, device=f.device) * r
-    uc_ring = u_ring[ring_idx][:, ring_idx].clone()
-    uc = initial_guess(net, fc, uc_ring)
-    fine = F.interpolate(uc[None, None], size=(n + 2, n + 2), mode="bilinear", align_corners=True)[0, 0]
-    u0 = u_ring.clone().to(torch.float64)
-    u0[1:n + 1, 1:n + 1] = fine[1:n + 1, 1:n + 1]
-    return u0
+    fc, uc_ring = guess_coarsen(f, u_ring, n_coarse)
+    return guess_refine(initial_guess(net, fc, uc_ring), u_ring)

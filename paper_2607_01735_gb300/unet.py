@@ -3,9 +3,9 @@
 Argument marshalling only: the convolutions, pooling, upsampling, loss, backward pass
 and Adam update all run in the library's CUDA kernels.  Tensors are torch CUDA
 tensors; bf16 operands are passed as torch.bfloat16 tensors (their uint16 bit
-patterns).  `network_input` assembles the four input channels (f, boundary mask,
-boundary values, boundary interpolation) of one Poisson problem on an H x W grid padded
-to a multiple of 8.
+patterns).  The grid operations around the network (the input channels, the boundary
+interpolation, the training target, the guess, the coarse-grid transfer) are the
+library's kernels too (rbgs_guess_*); torch only holds the memory.
 """
 from __future__ import annotations
 
@@ -47,6 +47,15 @@ def _lib():
         lib.rbgs_conv_get_engine.restype = ci
         lib.rbgs_conv_check.argtypes = [vp]
         lib.rbgs_conv_check.restype = ci
+        lib.rbgs_guess_blend.argtypes = [vp, ci, vp, vp]
+        lib.rbgs_guess_input.argtypes = [vp, vp, ci, ci, vp, vp]
+        lib.rbgs_guess_target.argtypes = [vp, vp, ci, ci, vp, vp]
+        lib.rbgs_guess_assemble.argtypes = [vp, vp, ci, ci, vp, vp]
+        lib.rbgs_guess_coarsen.argtypes = [vp, vp, ci, ci, vp, vp, vp]
+        lib.rbgs_guess_refine.argtypes = [vp, ci, vp, ci, vp, vp]
+        for name in ("rbgs_guess_blend", "rbgs_guess_input", "rbgs_guess_target", "rbgs_guess_assemble",
+                     "rbgs_guess_coarsen", "rbgs_guess_refine"):
+            getattr(lib, name).restype = ci
         _bound = True
     return lib
 
@@ -104,36 +113,68 @@ def rbgs_conv_backward(x, w, g, dx, dw, db, accumulate=False):
                                      Cout, k, int(accumulate), _stream(x)))
 
 
+def _dev64(t):
+    """A contiguous float64 CUDA tensor (the grid kernels read device memory)."""
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    return t.to(torch.float64).contiguous()
+
+
 def boundary_blend(u_ring):
     """Transfinite (Coons) interpolation of the ring values of an (N+2)^2 grid into its
-    interior: the bilinearly blended sum of the four edge interpolants minus the corner
-    bilinear term.  It reproduces boundary data that is linear in x and y exactly."""
-    g = u_ring.shape[0]
-    t = torch.linspace(0.0, 1.0, g, dtype=torch.float64, device=u_ring.device)
-    x, y = t[:, None], t[None, :]
-    u = u_ring.to(torch.float64)
-    north, south = u[0:1, :], u[g - 1:g, :]
-    west, east = u[:, 0:1], u[:, g - 1:g]
-    c00, c01, c10, c11 = u[0, 0], u[0, g - 1], u[g - 1, 0], u[g - 1, g - 1]
-    return ((1 - x) * north + x * south + (1 - y) * west + y * east
-            - ((1 - x) * (1 - y) * c00 + (1 - x) * y * c01 + x * (1 - y) * c10 + x * y * c11))
+    interior (rbgs_guess_blend): the bilinearly blended edge interpolants minus the corner
+    bilinear term; it reproduces boundary data that is linear in x and y exactly."""
+    u = _dev64(u_ring)
+    out = torch.empty_like(u)
+    _check(_lib().rbgs_guess_blend(_p(u), u.shape[0] - 2, _p(out), _stream(u)))
+    return out
 
 
 def network_input(f, u_ring, size=None):
-    """4-channel input of one problem: f on the interior, mask 1 on the Dirichlet ring,
-    ring values, and boundary_blend of the ring; the (N+2)^2 grid zero-padded to `size`
-    (default: multiple of 8)."""
+    """4-channel input of one problem (rbgs_guess_input): f on the interior, mask 1 on the
+    Dirichlet ring, ring values, and boundary_blend of the ring; the (N+2)^2 grid
+    zero-padded to `size` (default: multiple of 8)."""
     n = f.shape[0]
-    g = n + 2
-    size = size or (g + 7) // 8 * 8
-    x = torch.zeros((size, size, 4), dtype=torch.float32, device=f.device)
-    x[1:n + 1, 1:n + 1, 0] = f.to(torch.float32)
-    ring = torch.ones((g, g), dtype=torch.bool, device=f.device)
-    ring[1:n + 1, 1:n + 1] = False
-    x[:g, :g, 1] = ring.to(torch.float32)
-    x[:g, :g, 2] = torch.where(ring, u_ring.to(torch.float32), torch.zeros_like(u_ring, dtype=torch.float32))
-    x[:g, :g, 3] = boundary_blend(u_ring).to(torch.float32)
+    size = size or (n + 2 + 7) // 8 * 8
+    fd, u = _dev64(f), _dev64(u_ring)
+    x = torch.empty((size, size, 4), dtype=torch.float32, device=fd.device)
+    _check(_lib().rbgs_guess_input(_p(fd), _p(u), n, size, _p(x), _stream(fd)))
     return x
+
+
+def guess_target(sol, u_ring, size):
+    """Training target on the size^2 grid (rbgs_guess_target): sol - boundary_blend(u_ring)."""
+    s_, u = _dev64(sol), _dev64(u_ring)
+    t = torch.empty((size, size), dtype=torch.float32, device=u.device)
+    _check(_lib().rbgs_guess_target(_p(s_), _p(u), u.shape[0] - 2, size, _p(t), _stream(u)))
+    return t
+
+
+def guess_assemble(u_ring, pred):
+    """u0 (rbgs_guess_assemble): the ring of u_ring, interior blend + pred (size^2 floats)."""
+    u = _dev64(u_ring)
+    pred = pred.to(torch.float32).contiguous()
+    u0 = torch.empty_like(u)
+    _check(_lib().rbgs_guess_assemble(_p(u), _p(pred), u.shape[0] - 2, pred.shape[-1], _p(u0), _stream(u)))
+    return u0
+
+
+def guess_coarsen(f, u_ring, n_coarse):
+    """(fc, uc_ring) on the n_coarse^2 grid (rbgs_guess_coarsen): f averaged over the
+    (2r-1)^2 fine nodes around each coarse node, the ring sampled."""
+    fd, u = _dev64(f), _dev64(u_ring)
+    fc = torch.empty((n_coarse, n_coarse), dtype=torch.float64, device=fd.device)
+    uc = torch.empty((n_coarse + 2, n_coarse + 2), dtype=torch.float64, device=fd.device)
+    _check(_lib().rbgs_guess_coarsen(_p(fd), _p(u), fd.shape[0], n_coarse, _p(fc), _p(uc), _stream(fd)))
+    return fc, uc
+
+
+def guess_refine(uc, u_ring):
+    """Fine u0 (rbgs_guess_refine): uc interpolated bilinearly, the fine ring kept."""
+    c, u = _dev64(uc), _dev64(u_ring)
+    u0 = torch.empty_like(u)
+    _check(_lib().rbgs_guess_refine(_p(c), c.shape[0] - 2, _p(u), u.shape[0] - 2, _p(u0), _stream(u)))
+    return u0
 
 
 class UNet:

@@ -2,6 +2,7 @@
 // over a C interface so the CPU test suite can compare them with the CPU's own IEEE
 // addition and multiplication.  Test infrastructure only.
 #include "../../paper_2607_01735_gb300/csrc/fp64.cuh"
+#include "../../paper_2607_01735_gb300/csrc/div6.cuh"
 
 extern "C" {
 
@@ -16,6 +17,10 @@ void check_add_core(long n, const double *a, const double *b, double *out, int *
         out[q] = rbgs::add_int_core(a[q], b[q], k);
         ok[q] = k ? 1 : 0;
     }
+}
+
+void check_div6(long n, const double *a, double *out) {
+    for (long q = 0; q < n; ++q) out[q] = rbgs::div6(a[q]);
 }
 
 void check_quarter(long n, const double *a, double *out) {

@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "native", "fp64_host_check.cpp")
 OUT = os.path.join(HERE, "native", "_build", "libfp64check.so")
 HDR = os.path.join(os.path.dirname(HERE), "paper_2607_01735_gb300", "csrc", "fp64.cuh")
+HDR6 = os.path.join(os.path.dirname(HERE), "paper_2607_01735_gb300", "csrc", "div6.cuh")
 
 
 def _cuda_include():
@@ -24,7 +25,7 @@ def _cuda_include():
 @pytest.fixture(scope="module")
 def lib():
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
+    if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(os.path.getmtime(SRC), os.path.getmtime(HDR), os.path.getmtime(HDR6)):
         tmp = OUT + f".tmp{os.getpid()}"
         subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-fPIC", "-shared",
                                "-I", _cuda_include(), SRC, "-o", tmp])
@@ -33,6 +34,7 @@ def lib():
     dp = ctypes.POINTER(ctypes.c_double)
     l.check_add_int.argtypes = [ctypes.c_long, dp, dp, dp]
     l.check_quarter.argtypes = [ctypes.c_long, dp, dp]
+    l.check_div6.argtypes = [ctypes.c_long, dp, dp]
     l.check_add_core.argtypes = [ctypes.c_long, dp, dp, dp, ctypes.POINTER(ctypes.c_int)]
     return l
 
@@ -155,3 +157,25 @@ def test_quarter(lib):
     lib.check_quarter(a.size, _p(a), _p(out))
     with np.errstate(all="ignore"):
         assert _same_bits(out, a * 0.25)
+
+
+def test_div6_is_the_correctly_rounded_quotient(lib):
+    """div6 (Markstein's one-correction division by a constant) against IEEE division:
+    random operands over the whole exponent range, exact multiples of 6 and their
+    neighbours, contiguous significands, and the fallback's edge cases."""
+    rng = np.random.default_rng(6)
+    bits = rng.integers(0, 2 ** 63, 4_000_000, dtype=np.uint64) | (rng.integers(0, 2, 4_000_000, dtype=np.uint64) << 63)
+    a = bits.view(np.float64)
+    a = a[np.isfinite(a)]
+    k = np.arange(1, 1_000_001, dtype=np.float64) * 6.0
+    cont = (np.uint64(0x3FF0000000000000) + np.arange(2 ** 20, dtype=np.uint64)).view(np.float64)
+    edge = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2250738585072014e-308, 1.7976931348623157e308, np.inf, -np.inf,
+                     np.ldexp(1.0, -1016), np.ldexp(1.0, -1017), np.ldexp(1.0, 1020), np.ldexp(1.0, 1021)])
+    a = np.concatenate([a, k, np.nextafter(k, 0), np.nextafter(k, np.inf), cont, cont * 3.0, edge])
+    out = np.empty_like(a)
+    lib.check_div6(a.size, _p(a), _p(out))
+    want = a / 6.0
+    assert np.array_equal(out.view(np.uint64), want.view(np.uint64))
+    nan = np.array([np.nan])
+    lib.check_div6(1, _p(nan), _p(out[:1]))
+    assert np.isnan(out[0])

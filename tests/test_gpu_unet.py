@@ -6,11 +6,15 @@ Operands are bf16 on the GPU, so the oracle receives the same bf16-rounded input
 single-layer results then differ only by FP32 accumulation order (tolerance 1e-4 of
 the result scale).  The whole network stores bf16 activations and bf16 pre-activation
 gradients between layers; the oracle states the same roundings (unet_ref with
-bf16=True), so the forward output and every layer's weight and bias gradient are compared
-element by element.  What remains is FP32 accumulation order: an element whose value lies
-within that difference of a bf16 rounding boundary rounds to the neighbouring bf16 value
-on one side, and later layers carry such one-ulp steps along, so the tolerance is NET_TOL
-of the scale (the largest magnitude of the output, or of that layer's gradient block).
+bf16=True), and the forward output and every layer's weight and bias gradient are compared
+element by element at that block's own scale.  FP32 accumulation order still decides the
+bf16 rounding of elements that lie near a rounding boundary, and the ReLU mask of
+pre-activations within rounding of zero; such one-ulp or masked differences travel through
+later layers.  Measured on GB300 (64 x 64 inputs, seed 7): at most 1.4% of a block's scale
+per element (2.5% at 32 x 32, 14% at 16 x 16, where a level-2 weight gradient sums 32
+pixels only); hence 64 x 64 inputs and NET_TOL = 2% per element, 1% at the 99th
+percentile (fewer than 0.3% of a layer's elements exceeded 1% there), and the check that every layer is closer to the bf16 statement than to exact
+arithmetic (a misplaced or dropped block would be off by its whole scale).
 """
 import numpy as np
 import pytest
@@ -127,7 +131,8 @@ def test_conv_engines_agree(B, H, W, Cin, Cout, k):
             assert float((a - b).abs().max()) <= 1e-5 * scale + 1e-6
 
 
-NET_TOL = 1e-3
+NET_TOL = 2e-2          # per element, of the block's scale
+NET_TOL_P99 = 1e-2      # 99th percentile of the per-element error, of the block's scale
 
 
 def _f32(a):
@@ -135,31 +140,44 @@ def _f32(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
+_NET_CASE = {}
+
+
+def _network_case():
+    """The network test's inputs and both oracle gradients (computed once for all engines)."""
+    if not _NET_CASE:
+        from paper_2607_01735_gb300.unet import UNet
+        params = UNet(seed=7).get_params().cpu().double().numpy()  # FP32 master weights
+        rng = np.random.default_rng(5)
+        B, H, W = 2, 64, 64
+        x3 = _f32(rng.normal(size=(B, H, W, 4)))
+        target = _f32(rng.normal(size=(B, H, W)) * 0.1)
+        mask = (rng.uniform(size=(B, H, W)) > 0.2).astype(np.float64)
+        L_bf, g_bf = U.backward(params, x3, target, mask, bf16=True)
+        _, g_ex = U.backward(params, x3, target, mask, bf16=False)
+        _NET_CASE.update(x3=x3, target=target, mask=mask, L=L_bf, g=g_bf, g_exact=g_ex)
+    return _NET_CASE
+
+
 def test_network_gradient_matches_oracle(engine):
     from paper_2607_01735_gb300.unet import UNet
+    c = _network_case()
     net = UNet(seed=7)
-    params = net.get_params().cpu().double().numpy()   # FP32 master weights, exact in float64
-    rng = np.random.default_rng(5)
-    B, H, W = 2, 16, 16
-    x3 = _f32(rng.normal(size=(B, H, W, 4)))
-    target = _f32(rng.normal(size=(B, H, W)) * 0.1)
-    mask = (rng.uniform(size=(B, H, W)) > 0.2).astype(np.float64)
-    L_ref, g_ref = U.backward(params, x3, target, mask, bf16=True)
     grads = torch.empty(net.num_params, dtype=torch.float32, device="cuda")
-    L = net.train_step(torch.from_numpy(x3).float().cuda(), torch.from_numpy(target).float().cuda(),
-                       torch.from_numpy(mask).float().cuda(), lr=0.0, grads=grads)
+    L = net.train_step(torch.from_numpy(c["x3"]).float().cuda(), torch.from_numpy(c["target"]).float().cuda(),
+                       torch.from_numpy(c["mask"]).float().cuda(), lr=0.0, grads=grads)
     g = grads.cpu().double().numpy()
-    assert abs(L - L_ref) <= NET_TOL * L_ref, (L, L_ref)
-    # every layer's weights and biases, element by element at that block's own scale
+    assert abs(L - c["L"]) <= 1e-3 * c["L"], (L, c["L"])
     sl, _ = U.param_slices()
-    worst = []
     for li, (ws, bs, _) in enumerate(sl):
         for name, blk in (("w", ws), ("b", bs)):
-            scale = np.max(np.abs(g_ref[blk]))
-            err = np.max(np.abs(g[blk] - g_ref[blk]))
-            worst.append((err / scale, li, name))
-    worst.sort(reverse=True)
-    assert worst[0][0] <= NET_TOL, worst[:4]
+            ref, ex = c["g"][blk], c["g_exact"][blk]
+            scale = np.max(np.abs(ref))
+            err = np.abs(g[blk] - ref)
+            assert np.max(err) <= NET_TOL * scale, (li, name, np.max(err) / scale)
+            assert np.quantile(err, 0.99) <= NET_TOL_P99 * scale, (li, name, np.quantile(err, 0.99) / scale)
+            if name == "w":  # the library computes the bf16 statement, not exact arithmetic
+                assert np.max(err) < np.max(np.abs(g[blk] - ex)), li
     # padded input channels carry no gradient
     w0 = g[sl[0][0]].reshape(32, 3, 3, 16)
     assert np.all(w0[..., 4:] == 0)
@@ -175,12 +193,17 @@ def test_training_reduces_loss_and_forward_matches_oracle():
     m = torch.ones((B, H, W), device="cuda")
     losses = [net.train_step(x, t, m, lr=3e-3) for _ in range(150)]
     assert losses[-1] < 0.3 * losses[0]
-    # forward of the trained net vs the oracle stating the same bf16 storage, element by element
+    # forward of the trained net vs the oracle stating the same bf16 storage, element by
+    # element (measured: 3.1e-3 of the output's scale), and closer to it than to exact
+    # arithmetic
     p = net.get_params().cpu().double().numpy()
     y = net.forward(x).cpu().double().numpy()
-    y_ref = U.forward(p, x.cpu().double().numpy(), bf16=True)[..., 0]
-    err = np.max(np.abs(y - y_ref)) / np.max(np.abs(y_ref))
-    assert err <= NET_TOL, err
+    xin = x.cpu().double().numpy()
+    y_ref = U.forward(p, xin, bf16=True)[..., 0]
+    y_ex = U.forward(p, xin)[..., 0]
+    err = np.max(np.abs(y - y_ref))
+    assert err <= 1e-2 * np.max(np.abs(y_ref)), err / np.max(np.abs(y_ref))
+    assert err < np.max(np.abs(y - y_ex))
 
 
 @pytest.mark.slow
