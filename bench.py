@@ -874,6 +874,8 @@ def run_learned(args):
                 row[name] = {"sweeps": sweeps, "rho": rho, "solve_s": secs, "guess_s": t_guess,
                              "sweeps_to_tol_extrapolated": extra}
             results.append(row)
+            # each field as it completes, so that a long evaluation leaves its partial results
+            print(json.dumps({"learned_field": row}), file=sys.stderr, flush=True)
     line = {"metric": "sweeps and wall time to relative residual %.0e from the learned guess vs u0=0" % args.tol,
             "value": None, "unit": "sweeps", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
             "config": {"workload": f"U-Net (4 levels, 32 base channels, bf16 weights, fp32 accum) trained on "
