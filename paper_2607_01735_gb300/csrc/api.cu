@@ -255,13 +255,14 @@ rbgs_status ensure_graph(rbgs_ctx *c) {
 rbgs_status sweeps_f64(rbgs_ctx *c, long nsweeps) {
     if (c->fused) {
         // blocks of at most kFusedChunk sweeps, each at the scale chosen when it starts; the
-        // sweeps of a block as cached graphs of kGraphSweeps sweeps on small grids
+        // sweeps of a block as cached graphs of kGraphSweeps sweeps at every size (the
+        // half-sweeps are short even on large grids, so the launch gaps still count)
         while (nsweeps > 0) {
             long m = nsweeps < kFusedChunk ? nsweeps : kFusedChunk;
             nsweeps -= m;
             rbgs_status st = launch_fused_prepare(c, m, c->stream);
             if (st != RBGS_OK) return st;
-            if (c->g.n <= kGraphMaxN && m >= kGraphSweeps) {
+            if (m >= kGraphSweeps) {
                 if ((st = ensure_graph(c)) != RBGS_OK) return st;
                 while (m >= c->graph_sweeps) {
                     RBGS_CUDA(cudaGraphLaunch(c->graph, c->stream));
