@@ -784,11 +784,19 @@ def run_conv(args):
                        "engine": main_e, "l2": "per step all layers' operands, larger than L2 at the default size"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": f"conv_umma_kernel ({dom}: the product taking the most time), "
-                                   "of measured bf16 burst peak"},
+                         "kernel": f"{CONV_KERNELS.get((main_e, dom), 'conv_umma_kernel')} ({dom}: the product "
+                                   "taking the most time), of measured bf16 burst peak"},
             "engines": results, "clocks": clocks}
     print(json.dumps(line))
     return 0
+
+
+# the kernel that runs each product under each engine (3x3 layers)
+CONV_KERNELS = {("tcgen05", "fwd"): "conv_umma_kernel<0>", ("tcgen05", "dgrad"): "conv_tma_kernel<1>",
+                ("tcgen05", "wgrad"): "wgrad_shift_kernel", ("tcgen05_gather", "fwd"): "conv_umma_kernel<0>",
+                ("tcgen05_gather", "dgrad"): "conv_umma_kernel<1>", ("tcgen05_gather", "wgrad"): "conv_umma_kernel<2>",
+                ("mma_sync", "fwd"): "conv_igemm_kernel<FWD>", ("mma_sync", "dgrad"): "conv_igemm_kernel<BWD_DATA>",
+                ("mma_sync", "wgrad"): "conv_igemm_kernel<BWD_WEIGHT>"}
 
 
 def _solve_from(rb, n, h2, f, u0, tol, cap, chunk):

@@ -274,7 +274,7 @@ rbgs_status umma_conv_forward(const uint16_t *X, const uint16_t *Wt, const float
 rbgs_status umma_conv_backward_data(const uint16_t *Wtt, const uint16_t *G, float *dX, int B, int H, int W,
                                     int Cin, int Cout, int ks, int accumulate, bool tma, cudaStream_t s);
 rbgs_status umma_conv_backward_weight(const uint16_t *X, const uint16_t *G, float *dW, int B, int H, int W,
-                                      int Cin, int Cout, int ks, cudaStream_t s);
+                                      int Cin, int Cout, int ks, bool shift, cudaStream_t s);
 rbgs_status umma_conv_check(cudaStream_t s);
 
 rbgs_status conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y, int B, int H,
@@ -309,7 +309,8 @@ rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t 
         }
     }
     if (dW && g_engine != RBGS_CONV_MMA_SYNC) {
-        const rbgs_status st = umma_conv_backward_weight(X, G, dW, B, H, W, Cin, Cout, ks, s);
+        const rbgs_status st =
+            umma_conv_backward_weight(X, G, dW, B, H, W, Cin, Cout, ks, g_engine == RBGS_CONV_TCGEN05, s);
         if (st != RBGS_OK) return st;
     } else if (dW) {
         const int chunk = 4096;

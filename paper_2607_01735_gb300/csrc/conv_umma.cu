@@ -601,6 +601,7 @@ rbgs_status launch(const UArgs &a, cudaStream_t s) {
 bool sizes_fit(int B, int H, int W) { return (long)B * H * W < (1L << 31) - UK; }
 
 #include "conv_tma.cuh"
+#include "conv_wgrad.cuh"
 
 }  // namespace
 
@@ -642,10 +643,16 @@ rbgs_status umma_conv_backward_data(const uint16_t *Wtt, const uint16_t *G, floa
 }
 
 rbgs_status umma_conv_backward_weight(const uint16_t *X, const uint16_t *G, float *dW, int B, int H, int W,
-                                      int Cin, int Cout, int ks, cudaStream_t s) {
+                                      int Cin, int Cout, int ks, bool shift, cudaStream_t s) {
     if (!sizes_fit(B, H, W)) {
         set_error("tcgen05 convolution: at most 2^31 - 64 pixels");
         return RBGS_EINVAL;
+    }
+    // the tap shift in the descriptor (conv_wgrad.cuh); its epilogue adds 16-byte vectors
+    if (shift && ks == 3 && (reinterpret_cast<uintptr_t>(dW) & 15u) == 0) {
+        bool launched = false;
+        const rbgs_status st = wg_launch(X, G, dW, B, H, W, Cin, Cout, s, &launched);
+        if (st != RBGS_OK || launched) return st;
     }
     UArgs a{};
     a.X = X, a.G = G, a.out = dW;

@@ -48,7 +48,7 @@ ENGINES = {"tcgen05": 0, "mma_sync": 1, "tcgen05_gather": 2}
 # weight gradients split over several pixel chunks (4608 and 8192 pixels)
 CONV_SHAPES = [(2, 8, 8, 16, 32, 3), (1, 13, 11, 32, 64, 3), (2, 16, 16, 96, 32, 3), (3, 9, 7, 32, 8, 1),
                (1, 33, 40, 384, 128, 3), (1, 7, 5, 8, 48, 3), (2, 48, 48, 16, 256, 3), (2, 64, 64, 32, 16, 3),
-               (1, 10, 12, 256, 256, 1)]
+               (1, 10, 12, 256, 256, 1), (1, 6, 200, 32, 32, 3), (4, 64, 256, 32, 32, 3)]
 
 
 @pytest.fixture(params=list(ENGINES))
@@ -131,6 +131,43 @@ def test_conv_engines_agree(B, H, W, Cin, Cout, k):
             assert float((a - b).abs().max()) <= 1e-5 * scale + 1e-6
 
 
+# the 3x3 layer shapes of the network (Cin, Cout at their level's resolution), at batch 2
+# and a quarter of the training resolution
+UNET_3X3 = [(64, 16, 32), (64, 32, 32), (32, 32, 64), (32, 64, 64), (16, 64, 128), (16, 128, 128),
+            (8, 128, 256), (8, 256, 256), (16, 384, 128), (32, 192, 64), (64, 96, 32)]
+
+
+@pytest.mark.parametrize("hw,Cin,Cout", UNET_3X3)
+def test_weight_gradient_kernels_agree_on_network_layers(hw, Cin, Cout):
+    """The default engine's weight gradient (the tap shift taken in the shared-memory
+    descriptor; per layer either operand on the 128 TMEM lanes, one or two accumulator
+    buffers, several M or N tiles) against the gather kernel: the same FP32 sums of the same
+    bf16 products, up to accumulation order.  Run twice, so that dW accumulates."""
+    from paper_2607_01735_gb300 import unet as un
+    rng = np.random.default_rng(Cin * 7 + Cout)
+    x = _bf(rng.normal(size=(2, hw, hw, Cin))).cuda()
+    w = _bf(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin)).cuda()
+    g = _bf(rng.normal(size=(2, hw, hw, Cout))).cuda()
+    outs = {}
+    for name in ("tcgen05", "tcgen05_gather"):
+        un.rbgs_conv_set_engine(ENGINES[name])
+        dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
+        un.rbgs_conv_backward(x, w, g, None, dw, None)
+        un.rbgs_conv_backward(x, w, g, None, dw, None)
+        un.rbgs_conv_check()
+        outs[name] = dw
+    un.rbgs_conv_set_engine(un.RBGS_CONV_TCGEN05)
+    a, b = outs["tcgen05"], outs["tcgen05_gather"]
+    assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max())
+    # and the oracle on the first image's first rows (every tap and channel of dW)
+    X, G = x[:1, :4].double().cpu().numpy(), g[:1, :4].double().cpu().numpy()
+    dw1 = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
+    un.rbgs_conv_backward(x[:1, :4].contiguous(), w, g[:1, :4].contiguous(), None, dw1, None)
+    un.rbgs_conv_check()
+    _, ref, _ = U.conv_backward(X, w.double().cpu().numpy(), G)
+    assert np.max(np.abs(dw1.cpu().double().numpy() - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
 NET_TOL = 2e-2          # per element, of the block's scale
 NET_TOL_P99 = 1e-2      # 99th percentile of the per-element error, of the block's scale
 
@@ -194,16 +231,22 @@ def test_training_reduces_loss_and_forward_matches_oracle():
     losses = [net.train_step(x, t, m, lr=3e-3) for _ in range(150)]
     assert losses[-1] < 0.3 * losses[0]
     # forward of the trained net vs the oracle stating the same bf16 storage, element by
-    # element (measured: 3.1e-3 of the output's scale), and closer to it than to exact
-    # arithmetic
+    # element, on fresh 64 x 64 inputs, with the tolerances of the gradient test above, and
+    # closer to it than to exact arithmetic.  (At 16 x 16 the trained net's output moved by
+    # 0.3% to 2% of its scale from run to run: the FP32 atomics of training make every run's
+    # weights slightly different, and on so small a grid one pre-activation near a ReLU or
+    # bf16 rounding boundary shifts a large share of the output.)
     p = net.get_params().cpu().double().numpy()
-    y = net.forward(x).cpu().double().numpy()
-    xin = x.cpu().double().numpy()
+    x64 = torch.from_numpy(_f32(rng.normal(size=(2, 64, 64, 4)))).float().cuda()
+    y = net.forward(x64).cpu().double().numpy()
+    xin = x64.cpu().double().numpy()
     y_ref = U.forward(p, xin, bf16=True)[..., 0]
     y_ex = U.forward(p, xin)[..., 0]
-    err = np.max(np.abs(y - y_ref))
-    assert err <= 1e-2 * np.max(np.abs(y_ref)), err / np.max(np.abs(y_ref))
-    assert err < np.max(np.abs(y - y_ex))
+    err = np.abs(y - y_ref)
+    scale = np.max(np.abs(y_ref))
+    assert np.max(err) <= NET_TOL * scale, np.max(err) / scale
+    assert np.quantile(err, 0.99) <= NET_TOL_P99 * scale, np.quantile(err, 0.99) / scale
+    assert np.max(err) < np.max(np.abs(y - y_ex))
 
 
 @pytest.mark.slow
