@@ -94,8 +94,10 @@ def parse():
     p.add_argument("--conv-hw", type=int, default=256, help="conv: level-0 height = width")
     p.add_argument("--conv-layer", type=int, default=-1, help="conv: one layer index (-1: all 15)")
     p.add_argument("--conv-op", choices=["all", "fwd", "dgrad", "wgrad"], default="all")
-    p.add_argument("--engine", choices=["tcgen05", "mma_sync", "tcgen05_gather", "both", "all"], default="both",
-                   help="conv: engine(s) to time (both: tcgen05 and mma_sync; all: the three)")
+    p.add_argument("--engine", choices=["tcgen05", "mma_sync", "tcgen05_gather", "tcgen05_ring", "tcgen05_taprow",
+                                        "both", "all"], default="both",
+                   help="conv: engine(s) to time (both: tcgen05 and mma_sync; all: every engine, and the "
+                        "tcgen05 engine with each weight-gradient kernel forced)")
     p.add_argument("--mixed-n", type=int, default=8192, help="mixed: interior size")
     p.add_argument("--mixed-cap", type=int, default=20000, help="mixed: sweeps actually run per form")
     p.add_argument("--mixed-chunk", type=int, default=2000, help="mixed: sweeps between residual samples")
@@ -728,16 +730,24 @@ def run_conv(args):
     flop = 0.0
     for L in layers:
         flop += L["flop"] * (("fwd" in ops) + ("dgrad" in ops and L["dx"] is not None) + ("wgrad" in ops))
-    engines = {"both": ("tcgen05", "mma_sync"), "all": ("tcgen05", "mma_sync", "tcgen05_gather")}.get(
+    engines = {"both": ("tcgen05", "mma_sync"),
+               "all": ("tcgen05", "mma_sync", "tcgen05_gather", "tcgen05_ring", "tcgen05_taprow")}.get(
         args.engine, (args.engine,))
-    engine_ids = {"tcgen05": un.RBGS_CONV_TCGEN05, "mma_sync": un.RBGS_CONV_MMA_SYNC,
-                  "tcgen05_gather": un.RBGS_CONV_TCGEN05_GATHER}
+    # engine, and the tcgen05 engine's 3x3 weight-gradient kernel (the last two force one)
+    engine_ids = {"tcgen05": (un.RBGS_CONV_TCGEN05, un.RBGS_WGRAD_AUTO),
+                  "mma_sync": (un.RBGS_CONV_MMA_SYNC, un.RBGS_WGRAD_AUTO),
+                  "tcgen05_gather": (un.RBGS_CONV_TCGEN05_GATHER, un.RBGS_WGRAD_AUTO),
+                  "tcgen05_ring": (un.RBGS_CONV_TCGEN05, un.RBGS_WGRAD_RING),
+                  "tcgen05_taprow": (un.RBGS_CONV_TCGEN05, un.RBGS_WGRAD_TAPROW)}
     results = {}
     clocks = None
     peaks = measured_peaks() or {}
     peak = peaks.get("bf16_tflops", 1900.0)
+    peak_src = "measured bf16 burst peak (MEASURED_PEAKS.json)" if "bf16_tflops" in peaks else \
+        "fallback bf16 burst peak 1.9 PFLOP/s"
     for name in engines:
-        un.rbgs_conv_set_engine(engine_ids[name])
+        un.rbgs_conv_set_engine(engine_ids[name][0])
+        un.rbgs_conv_set_wgrad_kernel(engine_ids[name][1])
         for _ in range(args.warmup):
             step()
         un.rbgs_conv_check(dev)
@@ -771,6 +781,7 @@ def run_conv(args):
         if name == engines[0]:
             clocks = sampler.summary()
     un.rbgs_conv_set_engine(un.RBGS_CONV_TCGEN05)
+    un.rbgs_conv_set_wgrad_kernel(un.RBGS_WGRAD_AUTO)
     main_e = engines[0]
     r = results[main_e]
     # dominant product: the one taking the most time per step
@@ -785,7 +796,7 @@ def run_conv(args):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": f"{CONV_KERNELS.get((main_e, dom), 'conv_umma_kernel')} ({dom}: the product "
-                                   "taking the most time), of measured bf16 burst peak"},
+                                   "taking the most time)", "peak_source": peak_src},
             "engines": results, "clocks": clocks}
     print(json.dumps(line))
     return 0
@@ -793,7 +804,8 @@ def run_conv(args):
 
 # the kernel that runs each product under each engine (3x3 layers)
 CONV_KERNELS = {("tcgen05", "fwd"): "conv_umma_kernel<0>", ("tcgen05", "dgrad"): "conv_tma_kernel<1>",
-                ("tcgen05", "wgrad"): "wgrad_shift_kernel", ("tcgen05_gather", "fwd"): "conv_umma_kernel<0>",
+                ("tcgen05", "wgrad"): "wgrad_ring_kernel / wgrad_shift_kernel / conv_umma_kernel<2> (per layer)",
+                ("tcgen05_gather", "fwd"): "conv_umma_kernel<0>",
                 ("tcgen05_gather", "dgrad"): "conv_umma_kernel<1>", ("tcgen05_gather", "wgrad"): "conv_umma_kernel<2>",
                 ("mma_sync", "fwd"): "conv_igemm_kernel<FWD>", ("mma_sync", "dgrad"): "conv_igemm_kernel<BWD_DATA>",
                 ("mma_sync", "wgrad"): "conv_igemm_kernel<BWD_WEIGHT>"}

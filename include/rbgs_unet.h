@@ -80,6 +80,32 @@ int rbgs_conv_get_engine(void);
 
 /*
  * Not in the paper (learned initial guess): library mechanics.
+ * Kernel of the 3x3 weight-gradient product under RBGS_CONV_TCGEN05 (process-wide):
+ *   RBGS_WGRAD_AUTO   (default) per layer shape, the kernel that measured fastest on GB300
+ *                     over the network's layers: RBGS_WGRAD_RING for Cin <= 32;
+ *                     RBGS_WGRAD_TAPROW for image rows of at least 64 pixels when its work
+ *                     split gives every SM at least 40 stages; RBGS_WGRAD_GATHER otherwise;
+ *   RBGS_WGRAD_RING   all nine taps per stage: each activation row is staged once as three
+ *                     copies shifted by one pixel and kept in a ring while the output rows
+ *                     walk down the image (M = 3 Cin rows of (tap column, channel));
+ *   RBGS_WGRAD_TAPROW one tap row per pass: the activation row staged once with a pixel of
+ *                     halo, the three tap columns read at 16-byte descriptor offsets;
+ *   RBGS_WGRAD_GATHER the operand tiles gathered by cp.async per tap (the kernel that
+ *                     RBGS_CONV_TCGEN05_GATHER uses for every product).
+ * A kernel whose tiling does not fit a shape falls back to the next one in the order ring,
+ * tap row, gather.  All compute the same FP32 sums of the same bf16 products (the order of
+ * accumulation differs), and all add into dW.  Returns RBGS_EINVAL for another value.
+ * rbgs_conv_get_wgrad_kernel returns the current choice.  1x1 layers always gather.
+ */
+#define RBGS_WGRAD_AUTO 0
+#define RBGS_WGRAD_RING 1
+#define RBGS_WGRAD_TAPROW 2
+#define RBGS_WGRAD_GATHER 3
+rbgs_status rbgs_conv_set_wgrad_kernel(int kind);
+int rbgs_conv_get_wgrad_kernel(void);
+
+/*
+ * Not in the paper (learned initial guess): library mechanics.
  * Synchronises `cuda_stream` and reports whether a tcgen05 convolution launched since
  * the last check gave up one of its bounded waits on the tensor cores (RBGS_ETIMEOUT; its
  * output is then incomplete).  Clears the condition.  RBGS_OK otherwise.

@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(kBiasThreads) bias_grad_kernel(const uint16_t 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int g_engine = RBGS_CONV_TCGEN05;
+int g_wgrad_kind = RBGS_WGRAD_AUTO;
 
 }  // namespace
 
@@ -274,7 +275,7 @@ rbgs_status umma_conv_forward(const uint16_t *X, const uint16_t *Wt, const float
 rbgs_status umma_conv_backward_data(const uint16_t *Wtt, const uint16_t *G, float *dX, int B, int H, int W,
                                     int Cin, int Cout, int ks, int accumulate, bool tma, cudaStream_t s);
 rbgs_status umma_conv_backward_weight(const uint16_t *X, const uint16_t *G, float *dW, int B, int H, int W,
-                                      int Cin, int Cout, int ks, bool shift, cudaStream_t s);
+                                      int Cin, int Cout, int ks, int kind, cudaStream_t s);
 rbgs_status umma_conv_check(cudaStream_t s);
 
 rbgs_status conv_forward(const uint16_t *X, const uint16_t *Wt, const float *bias, void *Y, int B, int H,
@@ -309,8 +310,8 @@ rbgs_status conv_backward(const uint16_t *X, const uint16_t *Wt, const uint16_t 
         }
     }
     if (dW && g_engine != RBGS_CONV_MMA_SYNC) {
-        const rbgs_status st =
-            umma_conv_backward_weight(X, G, dW, B, H, W, Cin, Cout, ks, g_engine == RBGS_CONV_TCGEN05, s);
+        const rbgs_status st = umma_conv_backward_weight(
+            X, G, dW, B, H, W, Cin, Cout, ks, g_engine == RBGS_CONV_TCGEN05 ? g_wgrad_kind : RBGS_WGRAD_GATHER, s);
         if (st != RBGS_OK) return st;
     } else if (dW) {
         const int chunk = 4096;
@@ -371,6 +372,19 @@ extern "C" rbgs_status rbgs_conv_set_engine(int engine) {
 }
 
 extern "C" int rbgs_conv_get_engine(void) { return g_engine; }
+
+extern "C" rbgs_status rbgs_conv_set_wgrad_kernel(int kind) {
+    clear_error();
+    if (kind != RBGS_WGRAD_AUTO && kind != RBGS_WGRAD_RING && kind != RBGS_WGRAD_TAPROW &&
+        kind != RBGS_WGRAD_GATHER) {
+        set_error("rbgs_conv_set_wgrad_kernel: unknown kernel %d", kind);
+        return RBGS_EINVAL;
+    }
+    g_wgrad_kind = kind;
+    return RBGS_OK;
+}
+
+extern "C" int rbgs_conv_get_wgrad_kernel(void) { return g_wgrad_kind; }
 
 extern "C" rbgs_status rbgs_conv_check(void *cuda_stream) {
     clear_error();

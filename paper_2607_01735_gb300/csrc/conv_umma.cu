@@ -602,6 +602,7 @@ bool sizes_fit(int B, int H, int W) { return (long)B * H * W < (1L << 31) - UK; 
 
 #include "conv_tma.cuh"
 #include "conv_wgrad.cuh"
+#include "conv_wgrad_ring.cuh"
 
 }  // namespace
 
@@ -643,16 +644,32 @@ rbgs_status umma_conv_backward_data(const uint16_t *Wtt, const uint16_t *G, floa
 }
 
 rbgs_status umma_conv_backward_weight(const uint16_t *X, const uint16_t *G, float *dW, int B, int H, int W,
-                                      int Cin, int Cout, int ks, bool shift, cudaStream_t s) {
+                                      int Cin, int Cout, int ks, int kind, cudaStream_t s) {
     if (!sizes_fit(B, H, W)) {
         set_error("tcgen05 convolution: at most 2^31 - 64 pixels");
         return RBGS_EINVAL;
     }
-    // the tap shift in the descriptor (conv_wgrad.cuh); its epilogue adds 16-byte vectors
-    if (shift && ks == 3 && (reinterpret_cast<uintptr_t>(dW) & 15u) == 0) {
+    // 3x3 layers: the ring kernel (conv_wgrad_ring.cuh) or the tap-row kernel (conv_wgrad.cuh),
+    // whose epilogue adds 16-byte vectors, else the gather kernel below.  The automatic choice
+    // follows the per-layer measurements on GB300 (U-Net layers at 16 x 256^2, TFLOP/s, ring /
+    // tap row / gather): Cin <= 32, 256^2 and 128^2 rows: 88-166 / 45-144 / 75-157; the other
+    // layers with >= 40 tap-row stages per SM and rows >= 64 pixels: 326-514 (tap row) vs
+    // 163-273 (gather); the rest (stages per SM ~20, or 32-pixel rows): 234-317 (gather) vs
+    // 163-275 (tap row).
+    if (ks == 3 && kind != RBGS_WGRAD_GATHER && (reinterpret_cast<uintptr_t>(dW) & 15u) == 0) {
         bool launched = false;
-        const rbgs_status st = wg_launch(X, G, dW, B, H, W, Cin, Cout, s, &launched);
-        if (st != RBGS_OK || launched) return st;
+        rbgs_status st = RBGS_OK;
+        if (kind == RBGS_WGRAD_RING || (kind == RBGS_WGRAD_AUTO && Cin <= 32)) {
+            st = wr_launch(X, G, dW, B, H, W, Cin, Cout, s, &launched);
+            if (st != RBGS_OK || launched) return st;
+        }
+        WgPlan pl;
+        const bool fits = wg_plan(B, H, W, Cin, Cout, sm_count(), pl);
+        if (fits && (kind != RBGS_WGRAD_AUTO || (W >= 64 && pl.a.f_per_cta >= 40))) {
+            st = wg_launch(pl, X, G, dW, s);
+            if (st != RBGS_OK) return st;
+            return RBGS_OK;
+        }
     }
     UArgs a{};
     a.X = X, a.G = G, a.out = dW;

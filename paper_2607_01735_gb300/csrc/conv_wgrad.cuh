@@ -104,36 +104,49 @@ __device__ __forceinline__ void wg_combo(const WgArgs &a, int combo, int &ty, in
     nt = rest - mt * a.n_tiles;
 }
 
-// Unit walk of one staged row: units u = ptid, ptid + 256, ... of ng groups x npix pixels,
-// pixel-major so that a warp's copies read consecutive channels of consecutive pixels.
-struct WgWalk {
-    int p0, g0, dp, dg;
+// Staging tables: the 16-byte copies of one staged row that a producer thread issues, fixed
+// per launch (units u = ptid, ptid + 256, ... of the row; pixel-major with channel groups
+// fastest, so that a warp's copies read consecutive bytes of consecutive pixels).  Built
+// once per kernel, so a stage costs each copy an add, a bounds check and its address.
+constexpr int kWgMaxUnits = 8;
+
+struct WgUnits {
+    uint32_t dst[kWgMaxUnits];  // byte offset in the slot
+    int pc[kWgMaxUnits];        // pixel offset from the segment's first pixel (high 16 bits,
+                                // signed) and channel offset from the tile's first channel
+    int n;
 };
 
-__device__ __forceinline__ WgWalk wg_walk(int ng, int ptid) {
-    WgWalk w;
-    w.p0 = ptid / ng;
-    w.g0 = ptid - w.p0 * ng;
-    w.dp = kWgProducers / ng;
-    w.dg = kWgProducers - w.dp * ng;
-    return w;
+__device__ __forceinline__ int wg_pack_pc(int pix, int ch) { return (int)((uint32_t)pix << 16) | ch; }
+
+// Plain layout: unit (pixel p, group g) of ng groups x npix pixels at (g len + p) 16 bytes,
+// image pixel x0 + p + pix0.
+__device__ __forceinline__ WgUnits wg_units_plain(int ng, int npix, int len, int pix0, int ptid) {
+    WgUnits t;
+    t.n = 0;
+#pragma unroll
+    for (int k = 0; k < kWgMaxUnits; ++k) {
+        const int u = ptid + k * kWgProducers;
+        const int p = u / ng, g = u - p * ng;
+        t.dst[k] = (uint32_t)(g * len + p) * 16u;
+        t.pc[k] = wg_pack_pc(p + pix0, g * 8);
+        if (u < ng * npix) t.n = k + 1;
+    }
+    return t;
 }
 
-// Copies pixels xs .. xs + npix - 1 of one image row (channels c0 .. c0 + 8 ng - 1) into a
-// slot of ng groups x len pixel rows; pixels outside the row or the image, and channels
-// beyond C, are zero-filled.
-__device__ __forceinline__ void wg_stage_row(const uint16_t *row, bool row_ok, int C, int c0, int ng, int npix,
-                                             int len, int xs, int W, uint32_t slot, const WgWalk &w, int ptid) {
-    const int units = ng * npix;
-    int p = w.p0, g = w.g0;
-    for (int u = ptid; u < units; u += kWgProducers) {
-        const int x = xs + p;
-        const int c = c0 + g * 8;
-        const bool ok = row_ok && x >= 0 && x < W && c < C;
-        cp_async16(slot + (uint32_t)(g * len + p) * 16u, ok ? row + (long)x * C + c : row, ok);
-        p += w.dp;
-        g += w.dg;
-        if (g >= ng) g -= ng, ++p;
+// Issues a thread's copies of one staged row: image pixels x0 + pix, channels c0 + ch;
+// pixels outside the image row, channels beyond C and rows outside the image (row_ok
+// false) are zero-filled.
+__device__ __forceinline__ void wg_stage_units(const WgUnits &t, const uint16_t *row, bool row_ok, int C, int c0,
+                                               int x0, int W, uint32_t slot) {
+#pragma unroll
+    for (int k = 0; k < kWgMaxUnits; ++k) {
+        if (k < t.n) {
+            const int x = x0 + (t.pc[k] >> 16), c = c0 + (t.pc[k] & 0xFFFF);
+            const bool ok = row_ok && (unsigned)x < (unsigned)W && c < C;
+            cp_async16(slot + t.dst[k], ok ? row + (long)x * C + c : row, ok);
+        }
     }
 }
 
@@ -143,7 +156,8 @@ __device__ void wg_produce(const WgArgs &a, uint32_t sbase, uint64_t *full_bar, 
     const int S = a.stages;
     const int ngx = a.xa ? a.ngA : a.ngB, ngg = a.xa ? a.ngB : a.ngA;
     const int lenx = a.xa ? a.lenA : a.lenB, leng = a.xa ? a.lenB : a.lenA;
-    const WgWalk wx = wg_walk(ngx, ptid), wgw = wg_walk(ngg, ptid);
+    const WgUnits ux = wg_units_plain(ngx, a.seg + 2, lenx, -1, ptid);
+    const WgUnits ug = wg_units_plain(ngg, a.seg, leng, 0, ptid);
     uint32_t s = 0, ph = 0;
     bool live = true;
     WgItem it;
@@ -152,27 +166,32 @@ __device__ void wg_produce(const WgArgs &a, uint32_t sbase, uint64_t *full_bar, 
         wg_combo(a, it.combo, ty, mt, nt);
         const int xc0 = a.xa ? mt * 128 : nt * a.N;
         const int gc0 = a.xa ? nt * a.N : mt * 128;
+        // the item's first stage, then one segment (and row, image) further per stage
+        int r = it.s0 / a.nseg;
+        int sg = it.s0 - r * a.nseg;
+        int b = r / a.H, y = r - b * a.H;
         for (int j = 0; j < it.len; ++j) {
             if (!wait_or_abort(&empty_bar[s], ph ^ 1u, abort_flag)) {
                 live = false;
                 break;
             }
-            const int stage = it.s0 + j;
-            const int r = stage / a.nseg;
-            const int x0 = (stage - r * a.nseg) * a.seg;
-            const int b = r / a.H, y = r - b * a.H;
+            const int x0 = sg * a.seg;
             const uint32_t sa = sbase + s * a.a_slot, sb = sbase + a.b_ring + s * a.b_slot;
             const int yy = y + ty - 1;  // the activation row of this tap row
             const bool rx = yy >= 0 && yy < a.H;
             const uint16_t *xrow = a.X + (long)(b * a.H + (rx ? yy : y)) * a.W * a.Cin;
-            wg_stage_row(xrow, rx, a.Cin, xc0, ngx, a.seg + 2, lenx, x0 - 1, a.W, a.xa ? sa : sb, wx, ptid);
+            wg_stage_units(ux, xrow, rx, a.Cin, xc0, x0, a.W, a.xa ? sa : sb);
             const uint16_t *grow = a.G + (long)(b * a.H + y) * a.W * a.Cout;
-            wg_stage_row(grow, true, a.Cout, gc0, ngg, a.seg, leng, x0, a.W, a.xa ? sb : sa, wgw, ptid);
+            wg_stage_units(ug, grow, true, a.Cout, gc0, x0, a.W, a.xa ? sb : sa);
             // the stage's full barrier counts this thread's arrival once all its copies above
             // have landed; the thread itself moves on, so the whole ring can be in flight
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(&full_bar[s]))
                          : "memory");
             if (++s == (uint32_t)S) s = 0, ph ^= 1u;
+            if (++sg == a.nseg) {
+                sg = 0;
+                if (++y == a.H) y = 0, ++b;
+            }
         }
     }
     cp_async_wait<0>();
@@ -368,6 +387,9 @@ bool wg_plan(int B, int H, int W, int Cin, int Cout, int sms, WgPlan &pl) {
         const uint32_t as = (uint32_t)(a.ngA * lenA * 16), bs = (uint32_t)(a.ngB * lenB * 16);
         const uint32_t b_reach = (uint32_t)((16 * (nk - 1) + (a.xa ? 0 : 2)) * 16 + (a.ngB - 1) * lenB * 16 + 256);
         if (b_reach > bs) continue;
+        // every staged row fits the producers' unit tables
+        const int ngx = a.xa ? a.ngA : a.ngB, ngg = a.xa ? a.ngB : a.ngA;
+        if (ngx * (seg + 2) > kWgMaxUnits * kWgProducers || ngg * seg > kWgMaxUnits * kWgProducers) continue;
         for (int S = kWgMaxStages; S >= min_stages; --S) {
             const uint32_t rings = (uint32_t)S * (as + bs);
             const uint32_t a_reach =
@@ -406,18 +428,13 @@ bool wg_plan(int B, int H, int W, int Cin, int Cout, int sms, WgPlan &pl) {
     return true;
 }
 
-// Launches the shifted-descriptor weight gradient; *launched is false when no plan fits.
-rbgs_status wg_launch(const uint16_t *X, const uint16_t *G, float *dW, int B, int H, int W, int Cin, int Cout,
-                      cudaStream_t s, bool *launched) {
-    *launched = false;
-    WgPlan pl;
-    if (!wg_plan(B, H, W, Cin, Cout, sm_count(), pl)) return RBGS_OK;
+// Launches the tap-row weight gradient for a plan of wg_plan.
+rbgs_status wg_launch(WgPlan pl, const uint16_t *X, const uint16_t *G, float *dW, cudaStream_t s) {
     static const cudaError_t attr = cudaFuncSetAttribute(wgrad_shift_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          (int)(kWgBudget + 1024));
     RBGS_CUDA(attr);
     pl.a.X = X, pl.a.G = G, pl.a.dW = dW;
     wgrad_shift_kernel<<<pl.grid, kWgThreads, pl.smem, s>>>(pl.a);
     RBGS_LAUNCH_CHECK();
-    *launched = true;
     return RBGS_OK;
 }

@@ -45,6 +45,10 @@ def _lib():
         lib.rbgs_conv_set_engine.restype = ci
         lib.rbgs_conv_get_engine.argtypes = []
         lib.rbgs_conv_get_engine.restype = ci
+        lib.rbgs_conv_set_wgrad_kernel.argtypes = [ci]
+        lib.rbgs_conv_set_wgrad_kernel.restype = ci
+        lib.rbgs_conv_get_wgrad_kernel.argtypes = []
+        lib.rbgs_conv_get_wgrad_kernel.restype = ci
         lib.rbgs_conv_check.argtypes = [vp]
         lib.rbgs_conv_check.restype = ci
         lib.rbgs_guess_blend.argtypes = [vp, ci, vp, vp]
@@ -87,6 +91,23 @@ def rbgs_conv_set_engine(engine: int) -> None:
 
 def rbgs_conv_get_engine() -> int:
     return int(_lib().rbgs_conv_get_engine())
+
+
+RBGS_WGRAD_AUTO = 0
+RBGS_WGRAD_RING = 1
+RBGS_WGRAD_TAPROW = 2
+RBGS_WGRAD_GATHER = 3
+
+
+def rbgs_conv_set_wgrad_kernel(kind: int) -> None:
+    """Selects the 3x3 weight-gradient kernel of the tcgen05 engine process-wide:
+    RBGS_WGRAD_AUTO (per layer, the fastest measured), RBGS_WGRAD_RING, RBGS_WGRAD_TAPROW or
+    RBGS_WGRAD_GATHER."""
+    _check(_lib().rbgs_conv_set_wgrad_kernel(int(kind)))
+
+
+def rbgs_conv_get_wgrad_kernel() -> int:
+    return int(_lib().rbgs_conv_get_wgrad_kernel())
 
 
 def rbgs_conv_check(device=None) -> None:

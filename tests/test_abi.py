@@ -199,6 +199,14 @@ def test_unet_and_conv_argument_errors_without_gpu(lib):
     engine = lib.rbgs_conv_get_engine()
     assert lib.rbgs_conv_set_engine(i32(7)) == rb.RBGS_EINVAL
     assert lib.rbgs_conv_get_engine() == engine              # unchanged by a refused value
+    kind = lib.rbgs_conv_get_wgrad_kernel()
+    assert kind == 0                                         # RBGS_WGRAD_AUTO by default
+    assert lib.rbgs_conv_set_wgrad_kernel(i32(4)) == rb.RBGS_EINVAL
+    assert lib.rbgs_conv_set_wgrad_kernel(i32(-1)) == rb.RBGS_EINVAL
+    assert lib.rbgs_conv_get_wgrad_kernel() == kind
+    assert lib.rbgs_conv_set_wgrad_kernel(i32(2)) == rb.RBGS_OK
+    assert lib.rbgs_conv_get_wgrad_kernel() == 2
+    assert lib.rbgs_conv_set_wgrad_kernel(i32(0)) == rb.RBGS_OK
     assert lib.rbgs_unet_create(ctypes.c_uint64(1), None, None) == rb.RBGS_EINVAL
     lib.rbgs_unet_num_params.restype = ctypes.c_long
     assert lib.rbgs_unet_num_params(None) == 0

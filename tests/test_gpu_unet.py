@@ -42,23 +42,29 @@ def _bf(a):
 
 
 ENGINES = {"tcgen05": 0, "mma_sync": 1, "tcgen05_gather": 2}
+# the tcgen05 engine's 3x3 weight-gradient kernels (rbgs_conv_set_wgrad_kernel)
+WGRAD = {"auto": 0, "ring": 1, "taprow": 2, "gather": 3}
 
 # shapes: ragged pixel tiles (B H W not a multiple of 128), every N-tile width the
 # tcgen05 kernel picks (16 for Cout 8, 48, 192 for 384 = 2 x 192, 256), 1x1 kernels,
 # weight gradients split over several pixel chunks (4608 and 8192 pixels)
 CONV_SHAPES = [(2, 8, 8, 16, 32, 3), (1, 13, 11, 32, 64, 3), (2, 16, 16, 96, 32, 3), (3, 9, 7, 32, 8, 1),
                (1, 33, 40, 384, 128, 3), (1, 7, 5, 8, 48, 3), (2, 48, 48, 16, 256, 3), (2, 64, 64, 32, 16, 3),
-               (1, 10, 12, 256, 256, 1), (1, 6, 200, 32, 32, 3), (4, 64, 256, 32, 32, 3)]
+               (1, 10, 12, 256, 256, 1), (1, 6, 200, 32, 32, 3), (4, 64, 256, 32, 32, 3), (3, 1, 9, 32, 16, 3)]
 
 
-@pytest.fixture(params=list(ENGINES))
+@pytest.fixture(params=list(ENGINES) + ["tcgen05/ring", "tcgen05/taprow"])
 def engine(request):
+    """An engine, or the tcgen05 engine with one weight-gradient kernel forced."""
     from paper_2607_01735_gb300 import unet as un
     prev = un.rbgs_conv_get_engine()
-    un.rbgs_conv_set_engine(ENGINES[request.param])
+    name, _, wk = request.param.partition("/")
+    un.rbgs_conv_set_engine(ENGINES[name])
+    un.rbgs_conv_set_wgrad_kernel(WGRAD[wk or "auto"])
     yield request.param
     un.rbgs_conv_check()
     un.rbgs_conv_set_engine(prev)
+    un.rbgs_conv_set_wgrad_kernel(WGRAD["auto"])
 
 
 def test_engine_selection_rejects_unknown_values():
@@ -67,6 +73,10 @@ def test_engine_selection_rejects_unknown_values():
     with pytest.raises(rb.RbgsError):
         un.rbgs_conv_set_engine(7)
     assert un.rbgs_conv_get_engine() == un.RBGS_CONV_TCGEN05
+    assert un.rbgs_conv_get_wgrad_kernel() == un.RBGS_WGRAD_AUTO
+    with pytest.raises(rb.RbgsError):
+        un.rbgs_conv_set_wgrad_kernel(9)
+    assert un.rbgs_conv_get_wgrad_kernel() == un.RBGS_WGRAD_AUTO
 
 
 @pytest.mark.parametrize("B,H,W,Cin,Cout,k", CONV_SHAPES)
@@ -137,35 +147,62 @@ UNET_3X3 = [(64, 16, 32), (64, 32, 32), (32, 32, 64), (32, 64, 64), (16, 64, 128
             (8, 128, 256), (8, 256, 256), (16, 384, 128), (32, 192, 64), (64, 96, 32)]
 
 
+@pytest.mark.parametrize("kind", ["ring", "taprow", "auto"])
 @pytest.mark.parametrize("hw,Cin,Cout", UNET_3X3)
-def test_weight_gradient_kernels_agree_on_network_layers(hw, Cin, Cout):
-    """The default engine's weight gradient (the tap shift taken in the shared-memory
-    descriptor; per layer either operand on the 128 TMEM lanes, one or two accumulator
-    buffers, several M or N tiles) against the gather kernel: the same FP32 sums of the same
-    bf16 products, up to accumulation order.  Run twice, so that dW accumulates."""
+def test_weight_gradient_kernels_agree_on_network_layers(hw, Cin, Cout, kind):
+    """Each weight-gradient kernel of the tcgen05 engine (forced, or the per-layer automatic
+    choice; with their tilings: M tiles, N tiles, one or two accumulator buffers, either
+    operand on the 128 TMEM lanes) against the gather kernel on the network's layer shapes:
+    the same FP32 sums of the same bf16 products, up to accumulation order.  Run twice, so
+    that dW accumulates; and against the oracle on a slice of the input."""
     from paper_2607_01735_gb300 import unet as un
     rng = np.random.default_rng(Cin * 7 + Cout)
     x = _bf(rng.normal(size=(2, hw, hw, Cin))).cuda()
     w = _bf(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin)).cuda()
     g = _bf(rng.normal(size=(2, hw, hw, Cout))).cuda()
     outs = {}
-    for name in ("tcgen05", "tcgen05_gather"):
-        un.rbgs_conv_set_engine(ENGINES[name])
-        dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
-        un.rbgs_conv_backward(x, w, g, None, dw, None)
-        un.rbgs_conv_backward(x, w, g, None, dw, None)
+    try:
+        for name in (kind, "gather"):
+            un.rbgs_conv_set_wgrad_kernel(WGRAD[name])
+            dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
+            un.rbgs_conv_backward(x, w, g, None, dw, None)
+            un.rbgs_conv_backward(x, w, g, None, dw, None)
+            un.rbgs_conv_check()
+            outs[name] = dw
+        a, b = outs[kind], outs["gather"]
+        assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max())
+        # and the oracle on the first image's first rows (every tap and channel of dW)
+        un.rbgs_conv_set_wgrad_kernel(WGRAD[kind])
+        X, G = x[:1, :4].double().cpu().numpy(), g[:1, :4].double().cpu().numpy()
+        dw1 = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
+        un.rbgs_conv_backward(x[:1, :4].contiguous(), w, g[:1, :4].contiguous(), None, dw1, None)
         un.rbgs_conv_check()
-        outs[name] = dw
-    un.rbgs_conv_set_engine(un.RBGS_CONV_TCGEN05)
-    a, b = outs["tcgen05"], outs["tcgen05_gather"]
-    assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max())
-    # and the oracle on the first image's first rows (every tap and channel of dW)
-    X, G = x[:1, :4].double().cpu().numpy(), g[:1, :4].double().cpu().numpy()
-    dw1 = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
-    un.rbgs_conv_backward(x[:1, :4].contiguous(), w, g[:1, :4].contiguous(), None, dw1, None)
-    un.rbgs_conv_check()
-    _, ref, _ = U.conv_backward(X, w.double().cpu().numpy(), G)
-    assert np.max(np.abs(dw1.cpu().double().numpy() - ref)) <= 1e-4 * np.max(np.abs(ref))
+        _, ref, _ = U.conv_backward(X, w.double().cpu().numpy(), G)
+        assert np.max(np.abs(dw1.cpu().double().numpy() - ref)) <= 1e-4 * np.max(np.abs(ref))
+    finally:
+        un.rbgs_conv_set_wgrad_kernel(WGRAD["auto"])
+
+
+def test_weight_gradient_automatic_choice_on_full_size_layers():
+    """The automatic choice at the training batch's layer sizes (16 x 256^2 at level 0), where
+    it selects the ring, tap-row and gather kernels for different layers: it equals the
+    gather kernel's result up to accumulation order on one layer of each kind."""
+    from paper_2607_01735_gb300 import unet as un
+    for hw, Cin, Cout in ((256, 32, 32), (128, 64, 64), (64, 128, 128)):  # ring, tap row, gather
+        gen = torch.Generator(device="cuda").manual_seed(hw + Cin)
+        x = (torch.randn(16, hw, hw, Cin, generator=gen, device="cuda") * 0.5).to(torch.bfloat16)
+        w = (torch.randn(Cout, 3, 3, Cin, generator=gen, device="cuda") / (9 * Cin) ** 0.5).to(torch.bfloat16)
+        g = (torch.randn(16, hw, hw, Cout, generator=gen, device="cuda") * 0.1).to(torch.bfloat16)
+        outs = {}
+        for name in ("auto", "gather"):
+            un.rbgs_conv_set_wgrad_kernel(WGRAD[name])
+            dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device="cuda")
+            un.rbgs_conv_backward(x, w, g, None, dw, None)
+            un.rbgs_conv_check()
+            outs[name] = dw
+        un.rbgs_conv_set_wgrad_kernel(WGRAD["auto"])
+        a, b = outs["auto"], outs["gather"]
+        assert float((a - b).abs().max()) <= 1e-5 * float(b.abs().max()), (hw, Cin, Cout)
 
 
 NET_TOL = 2e-2          # per element, of the block's scale
