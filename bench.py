@@ -85,6 +85,8 @@ def parse():
     p.add_argument("--train-steps", type=int, default=3000, help="learned: Adam steps")
     p.add_argument("--eval-sizes", default="1023,4095", help="learned: held-out grid sizes")
     p.add_argument("--eval-fields", type=int, default=8, help="learned: held-out fields per size")
+    p.add_argument("--eval-first", type=int, default=0,
+                   help="learned: index k of the first held-out field (stream 5000 + 100 k + N mod 97)")
     p.add_argument("--eval-cap", default="5000000,20000000", help="learned: sweep cap per solve, per size")
     p.add_argument("--eval-starts", default="zero,coarse,full;zero,full",
                    help="learned: guesses solved from, per size (';'-separated)")
@@ -867,7 +869,7 @@ def run_learned(args):
     for si, n in enumerate(int(v) for v in args.eval_sizes.split(",")):
         cap = caps[min(si, len(caps) - 1)]
         h2 = synth.h_squared(n)
-        for k in range(args.eval_fields):
+        for k in range(args.eval_first, args.eval_first + args.eval_fields):
             stream = 5000 + 100 * k + n % 97
             f, u = synth.learned_guess_sample(n, stream)
             fd, ud = torch.from_numpy(f).cuda(), torch.from_numpy(u).cuda()
