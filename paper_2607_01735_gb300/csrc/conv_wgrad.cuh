@@ -28,8 +28,10 @@
 // Accumulators: the three taps of one tap row, 3 N TMEM columns (N <= 160), two buffers
 // where 6 N <= 512.  A work item is (tap row, M tile, N tile, run of stages).  The stage
 // sequence is cut into blocks of `lb` stages; within a block the items of every
-// (tap row, tile) follow one another, so the three tap rows of the same pixels run close
-// together in time and their re-reads of the activation rows come from L2.  The flattened
+// (tap row, tile) follow one another, so that the three tap rows of the same pixels run
+// close together in time and their re-reads of the activation rows can hit L2 (on a layer
+// whose inputs exceed L2, such as 96 channels at 16 x 256^2, they measured as DRAM reads,
+// three per input).  The flattened
 // (block, combination, stage) sequence is split evenly over the CTAs, and each CTA adds its
 // items' partial sums to dW with FP32 atomics (dW must hold zeros, or the sum to add to).
 //
